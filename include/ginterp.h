@@ -1,0 +1,160 @@
+/*
+ * ginterp.h -- C ABI of the GB300 G-Interp library (libginterp.so).
+ *
+ * G-Interp is the interpolation predictor-quantizer of the cuSZ-i lossy
+ * compressor (arXiv 2312.05492, Sec. IV): anchors on a stride-8 grid are
+ * stored losslessly (Sec. IV-A); the remaining points are predicted level by
+ * level at strides 4, 2, 1, one axis at a time, by linear / quadratic / cubic
+ * splines chosen by neighbour count (Sec. IV-B.1, Fig. 3) from already
+ * reconstructed values; each residual is quantized against a level-wise error
+ * bound (Sec. IV-B.1) into a 16-bit quant-code, codes too large for the
+ * radius R become outliers (Sec. III-A) gathered by stream compaction
+ * (Sec. V-A), and the codes are histogrammed (Fig. 1, Sec. V-A).
+ * Decompression replays the same order (Sec. IV-B.1).
+ *
+ * Conventions for every entry point:
+ *   - Fields are float32, C-contiguous, dims = {nz, ny, nx} with x fastest:
+ *     index i = (z*ny + y)*nx + x.  1 <= each dim, N = nz*ny*nx < 2^32.
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
+ *     are host pointers.  The caller allocates and owns every buffer; the
+ *     library never allocates, frees or synchronises (except interp_autotune).
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is stream-ordered.  Input buffers are not modified.
+ *   - Return value: INTERP_OK, or a negative interp_status for argument
+ *     errors (detected on the host before anything is enqueued) and launch
+ *     errors.  Conditions found on the device are reported in
+ *     interp_header.status (bit flags INTERP_STATUS_*).
+ *   - Level index l = 0, 1, 2 refers to strides 1, 2, 4 (the paper's level
+ *     ell = l + 1); per-level arrays are indexed by l.
+ */
+#ifndef GINTERP_H
+#define GINTERP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *interp_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    INTERP_OK = 0,
+    INTERP_EINVAL = -1,     /* bad argument (dims, eb, radius, order, null pointer, ...) */
+    INTERP_ECUDA = -2,      /* a CUDA launch or runtime call failed */
+    INTERP_EWORKSPACE = -3, /* workspace smaller than interp_workspace_bytes() */
+    INTERP_ECAPACITY = -4,  /* (host helper) outlier count exceeds out_capacity */
+    INTERP_ENONFINITE = -5  /* (host helper) non-finite input values were found */
+} interp_status;
+
+/* device-side status bits (interp_header.status) */
+#define INTERP_STATUS_CAPACITY 1u  /* more outliers than out_capacity; n_outliers is the true count */
+#define INTERP_STATUS_NONFINITE 2u /* the field holds NaN/Inf (stored losslessly as outliers) */
+
+/* Interpolation configuration (Sec. IV-B). */
+typedef struct {
+    int32_t dim_order[3];  /* permutation of {0=z, 1=y, 2=x}; dim_order[0] is interpolated
+                              first in every level (Sec. IV-B.2: least smooth axis first) */
+    int32_t level_kind[3]; /* per level l (stride 2^l): 0 = linear spline only,
+                              1 = splines by neighbour count (cubic/quadratic/linear) */
+    int32_t cubic_kind[3]; /* per axis: 0 = not-a-knot cubic, 1 = natural cubic */
+    int32_t eb_mode;       /* 0 = eb is absolute, 1 = eb is relative to the value range */
+    int32_t autotune;      /* 1 = dim_order, cubic_kind and level_kind are chosen on the
+                              device from a 4x4x4 sampling profile (Sec. IV-B.2) */
+    int32_t radius;        /* R: codes q with |q| < R are kept, others become outliers;
+                              2 <= R <= 32768 (codes are uint16, code 0 marks an outlier) */
+    double alpha;          /* error-bound reduction factor; <= 0 selects Eq. 1 A(eps) in
+                              relative mode and 1 in absolute mode */
+} interp_config;
+
+/* Written on the device by interp_compress; read by interp_decompress. */
+typedef struct {
+    int64_t dims[3];
+    interp_config cfg;     /* effective configuration (after autotuning) */
+    double eb;             /* eb as passed by the caller */
+    double eb_abs;         /* absolute bound e = eps * (vmax - vmin) or eb */
+    double alpha;          /* effective alpha */
+    float e[3];            /* level bounds e_l = e / alpha^l (Sec. IV-B.1) */
+    float twoe[3];         /* 2 e_l: quantization bin width */
+    float inv2e[3];        /* float(1 / (2 e_l)) */
+    float vmin, vmax;      /* finite value range (relative mode) */
+    uint64_t n_outliers;   /* true number of outliers */
+    uint64_t n_nonfinite;  /* non-finite input values (relative mode) */
+    uint32_t status;       /* INTERP_STATUS_* bits */
+    uint32_t reserved;
+    double profile[18];    /* sampling-profile error sums (autotune) */
+} interp_header;
+
+/* Number of anchor points: prod over axes of (floor((n_d - 1) / 8) + 1) (Sec. IV-A).
+ * Returns 0 for invalid dims. */
+size_t interp_anchor_count(const int64_t dims[3]);
+
+/* Device scratch that interp_compress needs, in bytes (0 for invalid args). */
+size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg);
+
+/* Compress a float32 field (Sec. IV-A/B, Sec. V-A).
+ *   d_x          [N] input field (read only)
+ *   dims         host array {nz, ny, nx}
+ *   eb           error bound: absolute, or relative to (max - min) when cfg->eb_mode = 1
+ *   cfg          host pointer to the configuration (copied; not retained)
+ *   d_anchors    [interp_anchor_count(dims)] out: x at points with all coords = 0 mod 8,
+ *                laid out [nz'][ny'][nx'] with n' = floor((n - 1)/8) + 1
+ *   d_codes      [N] out: uint16 quant-codes; q + R for kept points, 0 for outliers,
+ *                R at anchors
+ *   d_out_idx,
+ *   d_out_val    [out_capacity] out: outlier indices (ascending) and original values;
+ *                if the true count exceeds out_capacity only the first out_capacity
+ *                are written and INTERP_STATUS_CAPACITY is set
+ *   d_hist       [2R] out or NULL: histogram of d_codes (zeroed by the callee)
+ *   d_hdr        out: device header (bounds, effective config, counts, status)
+ *   d_ws         device scratch of ws_bytes >= interp_workspace_bytes(dims, cfg)
+ * Guarantee: for every point |x - x'| <= e_l of its level <= eb_abs, where x' is the
+ * output of interp_decompress; anchors and outliers are exact. */
+int interp_compress(const float *d_x, const int64_t dims[3], double eb, const interp_config *cfg,
+                    float *d_anchors, uint16_t *d_codes, uint32_t *d_out_idx, float *d_out_val,
+                    uint64_t out_capacity, uint32_t *d_hist, interp_header *d_hdr,
+                    void *d_ws, size_t ws_bytes, interp_stream_t stream);
+
+/* Decompress (Sec. IV-B.1: replay of the prediction from the quant-codes).
+ *   dims must equal the dims the field was compressed with (the caller keeps
+ *   them; they are also in the header); d_hdr, d_anchors, d_codes, d_out_idx,
+ *   d_out_val as written by interp_compress, with out_capacity entries
+ *   available (the first min(n_outliers, out_capacity) are scattered);
+ *   d_xrec [N] out.  No workspace is needed. */
+int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const float *d_anchors,
+                      const uint16_t *d_codes, const uint32_t *d_out_idx, const float *d_out_val,
+                      uint64_t out_capacity, float *d_xrec, interp_stream_t stream);
+
+/* Histogram of quant-codes (Fig. 1 "histogram", Sec. V-A): d_hist[c] = #{i : codes[i] = c}
+ * for c in [0, 2R); d_hist (2R uint32) is zeroed by the callee.  Codes >= 2R are ignored. */
+int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_t *d_hist,
+                    interp_stream_t stream);
+
+/* Sampling profile and decision (Sec. IV-B.1 data profiling, Sec. IV-B.2 auto-tuning):
+ * fills h_cfg->dim_order, cubic_kind and level_kind from the 4x4x4 sample profile of
+ * d_x and writes the 18 profile sums to h_profile (may be NULL).  Uses 512 bytes of
+ * d_ws.  SYNCHRONISES the stream (one small device-to-host copy). */
+int interp_autotune(const float *d_x, const int64_t dims[3], interp_config *h_cfg,
+                    double *h_profile, void *d_ws, size_t ws_bytes, interp_stream_t stream);
+
+/* Measurement support (not part of the compression method): while enabled,
+ * every interp_compress / interp_decompress call records a pair of CUDA events
+ * on its stream immediately around its tile kernel (at most 512 pairs per kernel;
+ * later calls are not recorded).  interp_timing_enable(1) clears previous
+ * records, (0) stops recording.  interp_timing_read waits for the recorded
+ * events and returns the summed milliseconds and launch counts of the
+ * compression and decompression tile kernels (any pointer may be NULL).
+ * Process-wide state for the current device; not thread-safe. */
+int interp_timing_enable(int on);
+int interp_timing_read(double *compress_ms, int32_t *compress_launches, double *decompress_ms,
+                       int32_t *decompress_launches);
+
+/* Human-readable text for an interp_status value. */
+const char *interp_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GINTERP_H */

@@ -1,0 +1,270 @@
+// C ABI of libginterp.so (declared in include/ginterp.h): argument checks,
+// workspace layout and the stream-ordered launch sequences of compression
+// (profile -> range/bounds -> tiles -> outlier compaction) and decompression
+// (outlier scatter -> tiles).
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace gi {
+size_t range_partials_bytes();
+}
+
+namespace {
+
+using gi::Dims;
+
+constexpr size_t kAlign = 256;
+constexpr size_t kCtrlBytes = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool dims_ok(const int64_t *dims)
+{
+    if (!dims) return false;
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (int64_t)0x7fffffff) return false;
+    const double n = (double)dims[0] * (double)dims[1] * (double)dims[2];
+    return n < 4294967296.0;  // u32 outlier indices
+}
+
+bool cfg_ok(const interp_config *c)
+{
+    if (!c) return false;
+    int seen = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (c->dim_order[a] < 0 || c->dim_order[a] > 2) return false;
+        seen |= 1 << c->dim_order[a];
+        if (c->level_kind[a] != 0 && c->level_kind[a] != 1) return false;
+        if (c->cubic_kind[a] != 0 && c->cubic_kind[a] != 1) return false;
+    }
+    if (seen != 7) return false;
+    if (c->eb_mode != 0 && c->eb_mode != 1) return false;
+    if (c->autotune != 0 && c->autotune != 1) return false;
+    if (c->radius < 2 || c->radius > 32768) return false;
+    if (std::isnan(c->alpha) || std::isinf(c->alpha)) return false;
+    return true;
+}
+
+int64_t bitmap_words(const int64_t *dims) { return dims[0] * dims[1] * ((dims[2] + 31) / 32); }
+
+struct WsLayout {
+    size_t ctrl, partials, bitmap, blockcnt, total;
+    int64_t words;
+    int nblk;
+};
+
+WsLayout ws_layout(const int64_t *dims)
+{
+    WsLayout L;
+    L.words = bitmap_words(dims);
+    L.nblk = (int)((L.words + gi::BITMAP_BLOCK_WORDS - 1) / gi::BITMAP_BLOCK_WORDS);
+    L.ctrl = 0;
+    L.partials = kCtrlBytes;
+    L.bitmap = align_up(L.partials + gi::range_partials_bytes());
+    L.blockcnt = align_up(L.bitmap + sizeof(uint32_t) * (size_t)L.words);
+    L.total = align_up(L.blockcnt + sizeof(uint32_t) * (size_t)L.nblk);
+    return L;
+}
+
+// Eq. 1 (Sec. IV-B.2): alpha = A(eps), piecewise linear in the relative bound.
+double alpha_of_eps(double eps)
+{
+    if (eps >= 1e-1) return 2.0;
+    if (eps >= 1e-2) return 1.75 + 0.25 * (eps - 1e-2) / (1e-1 - 1e-2);
+    if (eps >= 1e-3) return 1.5 + 0.25 * (eps - 1e-3) / (1e-2 - 1e-3);
+    if (eps >= 1e-4) return 1.25 + 0.25 * (eps - 1e-4) / (1e-3 - 1e-4);
+    if (eps >= 1e-5) return 1.0 + 0.25 * (eps - 1e-5) / (1e-4 - 1e-5);
+    return 1.0;
+}
+
+double effective_alpha(const interp_config &c, double eb)
+{
+    if (c.alpha > 0) return c.alpha;
+    return c.eb_mode ? alpha_of_eps(eb) : 1.0;
+}
+
+Dims to_dims(const int64_t *d) { return Dims{(int)d[0], (int)d[1], (int)d[2]}; }
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? INTERP_OK : INTERP_ECUDA; }
+
+// ---- optional event timing around the tile kernels (measurement only)
+constexpr int kTimingPairs = 512;
+struct TimingLog {
+    cudaEvent_t ev[2][kTimingPairs][2];
+    int used[2];
+    bool created;
+    bool on;
+};
+TimingLog g_timing{};
+
+void timing_mark(int kind, int edge, cudaStream_t s)
+{
+    if (!g_timing.on) return;
+    const int i = g_timing.used[kind];
+    if (i >= kTimingPairs) return;
+    cudaEventRecord(g_timing.ev[kind][i][edge], s);
+    if (edge == 1) g_timing.used[kind] = i + 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t interp_anchor_count(const int64_t dims[3])
+{
+    if (!dims_ok(dims)) return 0;
+    size_t n = 1;
+    for (int a = 0; a < 3; ++a) n *= (size_t)((dims[a] - 1) / 8 + 1);
+    return n;
+}
+
+size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg)
+{
+    if (!dims_ok(dims) || !cfg_ok(cfg)) return 0;
+    return ws_layout(dims).total;
+}
+
+int interp_compress(const float *d_x, const int64_t dims[3], double eb, const interp_config *cfg,
+                    float *d_anchors, uint16_t *d_codes, uint32_t *d_out_idx, float *d_out_val,
+                    uint64_t out_capacity, uint32_t *d_hist, interp_header *d_hdr, void *d_ws, size_t ws_bytes,
+                    interp_stream_t stream)
+{
+    if (!dims_ok(dims) || !cfg_ok(cfg)) return INTERP_EINVAL;
+    if (!(eb > 0.0) || std::isinf(eb)) return INTERP_EINVAL;
+    if (!d_x || !d_anchors || !d_codes || !d_hdr || !d_ws) return INTERP_EINVAL;
+    if (out_capacity > 0 && (!d_out_idx || !d_out_val)) return INTERP_EINVAL;
+    const WsLayout L = ws_layout(dims);
+    if (ws_bytes < L.total) return INTERP_EWORKSPACE;
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const interp_config c = *cfg;
+    const Dims d = to_dims(dims);
+    const double alpha = effective_alpha(c, eb);
+    unsigned char *ws = static_cast<unsigned char *>(d_ws);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(ws + L.ctrl);
+    uint32_t *bitmap = reinterpret_cast<uint32_t *>(ws + L.bitmap);
+    uint32_t *blockcnt = reinterpret_cast<uint32_t *>(ws + L.blockcnt);
+
+    cudaError_t e = cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(blockcnt, 0, sizeof(uint32_t) * (size_t)L.nblk, s);
+    if (e == cudaSuccess && d_hist) e = cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * 2 * (size_t)c.radius, s);
+    if (e == cudaSuccess && c.autotune) e = gi::launch_profile(d_x, d, d_hdr, 1, s);
+    if (e == cudaSuccess) {
+        if (c.eb_mode)
+            e = gi::launch_range(d_x, d, eb, c, alpha, d_hdr, ws + L.partials, counter, gi::range_blocks(), s);
+        else
+            e = gi::launch_header_init(d_hdr, d, eb, c, alpha, s);
+    }
+    if (e == cudaSuccess) {
+        gi::CompressArgs a{d_x, d, d_anchors, d_codes, bitmap, blockcnt, d_hist, c.radius, d_hdr,
+                           gi::aligned16(d_x) && d.nx % 4 == 0, gi::aligned16(d_codes) && d.nx % 8 == 0};
+        timing_mark(0, 0, s);
+        e = gi::launch_compress_tiles(a, s);
+        timing_mark(0, 1, s);
+    }
+    if (e == cudaSuccess)
+        e = gi::launch_outlier_compaction(bitmap, blockcnt, L.words, d, d_x, d_out_idx, d_out_val, out_capacity,
+                                          d_hdr, s);
+    return cuda_status(e);
+}
+
+int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const float *d_anchors,
+                      const uint16_t *d_codes, const uint32_t *d_out_idx, const float *d_out_val,
+                      uint64_t out_capacity, float *d_xrec, interp_stream_t stream)
+{
+    if (!dims_ok(dims)) return INTERP_EINVAL;
+    if (!d_hdr || !d_anchors || !d_codes || !d_xrec) return INTERP_EINVAL;
+    if (out_capacity > 0 && (!d_out_idx || !d_out_val)) return INTERP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Dims d = to_dims(dims);
+    cudaError_t e = cudaSuccess;
+    if (out_capacity > 0) e = gi::launch_outlier_scatter(d_hdr, d_out_idx, d_out_val, out_capacity, d_xrec, s);
+    if (e == cudaSuccess) {
+        gi::DecompressArgs a{d, d_anchors, d_codes, d_xrec, d_hdr, gi::aligned16(d_codes) && d.nx % 8 == 0,
+                             gi::aligned16(d_xrec) && d.nx % 4 == 0};
+        timing_mark(1, 0, s);
+        e = gi::launch_decompress_tiles(a, s);
+        timing_mark(1, 1, s);
+    }
+    return cuda_status(e);
+}
+
+int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_t *d_hist, interp_stream_t stream)
+{
+    if (radius < 2 || radius > 32768 || !d_hist || (n > 0 && !d_codes)) return INTERP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * 2 * (size_t)radius, s);
+    if (e == cudaSuccess && n > 0) e = gi::launch_histogram(d_codes, n, radius, d_hist, s);
+    return cuda_status(e);
+}
+
+int interp_autotune(const float *d_x, const int64_t dims[3], interp_config *h_cfg, double *h_profile, void *d_ws,
+                    size_t ws_bytes, interp_stream_t stream)
+{
+    if (!dims_ok(dims) || !h_cfg || !d_x || !d_ws) return INTERP_EINVAL;
+    if (ws_bytes < sizeof(interp_header)) return INTERP_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    interp_header *tmp = static_cast<interp_header *>(d_ws);
+    cudaError_t e = gi::launch_profile(d_x, to_dims(dims), tmp, 1, s);
+    interp_header h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, tmp, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return INTERP_ECUDA;
+    for (int a = 0; a < 3; ++a) {
+        h_cfg->dim_order[a] = h.cfg.dim_order[a];
+        h_cfg->cubic_kind[a] = h.cfg.cubic_kind[a];
+        h_cfg->level_kind[a] = h.cfg.level_kind[a];
+    }
+    if (h_profile) std::memcpy(h_profile, h.profile, sizeof(h.profile));
+    return INTERP_OK;
+}
+
+int interp_timing_enable(int on)
+{
+    if (on && !g_timing.created) {
+        for (int k = 0; k < 2; ++k)
+            for (int i = 0; i < kTimingPairs; ++i)
+                for (int j = 0; j < 2; ++j)
+                    if (cudaEventCreate(&g_timing.ev[k][i][j]) != cudaSuccess) return INTERP_ECUDA;
+        g_timing.created = true;
+    }
+    if (on) g_timing.used[0] = g_timing.used[1] = 0;
+    g_timing.on = on != 0;
+    return INTERP_OK;
+}
+
+int interp_timing_read(double *compress_ms, int32_t *compress_launches, double *decompress_ms,
+                       int32_t *decompress_launches)
+{
+    double ms[2] = {0.0, 0.0};
+    for (int k = 0; k < 2 && g_timing.created; ++k)
+        for (int i = 0; i < g_timing.used[k]; ++i) {
+            if (cudaEventSynchronize(g_timing.ev[k][i][1]) != cudaSuccess) return INTERP_ECUDA;
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, g_timing.ev[k][i][0], g_timing.ev[k][i][1]) != cudaSuccess)
+                return INTERP_ECUDA;
+            ms[k] += t;
+        }
+    if (compress_ms) *compress_ms = ms[0];
+    if (compress_launches) *compress_launches = g_timing.used[0];
+    if (decompress_ms) *decompress_ms = ms[1];
+    if (decompress_launches) *decompress_launches = g_timing.used[1];
+    return INTERP_OK;
+}
+
+const char *interp_status_string(int status)
+{
+    switch (status) {
+    case INTERP_OK: return "ok";
+    case INTERP_EINVAL: return "invalid argument";
+    case INTERP_ECUDA: return "CUDA error";
+    case INTERP_EWORKSPACE: return "workspace too small";
+    case INTERP_ECAPACITY: return "outlier capacity exceeded";
+    case INTERP_ENONFINITE: return "non-finite input";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

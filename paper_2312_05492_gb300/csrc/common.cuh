@@ -1,0 +1,146 @@
+// Shared device-side definitions of the G-Interp CUDA library (sm_103a).
+//
+// Every kernel is compiled with --fmad=false: each float operation below is
+// rounded on its own, in the order written, so the quant-codes and the
+// reconstruction are reproducible bit for bit.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "ginterp.h"
+
+namespace gi {
+
+// ----------------------------------------------------------- tile geometry
+// A CTA works on a tile of TZ x TY x TX chunks of 8^3 points (Sec. IV-A),
+// staged in shared memory together with the closing faces at the far end of
+// each axis (the "borrowed" anchors and face points of the neighbouring
+// chunks, Sec. IV-C), i.e. a (8TZ+1) x (8TY+1) x (8TX+1) box.
+constexpr int TZ = 2, TY = 2, TX = 4;
+constexpr int OZ = 8 * TZ, OY = 8 * TY, OX = 8 * TX;  // owned extent
+constexpr int BZ = OZ + 1, BY = OY + 1, BX = OX + 1;  // box extent (with far faces)
+constexpr int BOX = BZ * BY * BX;
+constexpr int OWN = OZ * OY * OX;
+constexpr int TILE_THREADS = 256;
+static_assert(OX == 32, "one outlier-bitmap word covers the 32 x-positions of an owned row");
+
+// outlier bitmap: one 32-bit word per 32 x-positions of every (z, y) row
+constexpr int BITMAP_BLOCK_WORDS = 2048;  // words per compaction block
+
+// histogram bins kept in shared memory by the fused histogram
+constexpr int HIST_SMEM_BINS = 1024;
+
+// ------------------------------------------------------------- parameters
+struct Dims {
+    int nz, ny, nx;
+};
+
+struct TileGrid {
+    int tz, ty, tx;  // tiles per axis
+};
+
+// ---------------------------------------------------------------- splines
+// p for the neighbour sets of Sec. IV-B.1; m3, m1, p1, p3 = x_{n-3s}, x_{n-s},
+// x_{n+s}, x_{n+3s}.
+__device__ __forceinline__ float sp_linear(float m1, float p1) { return (m1 + p1) * 0.5f; }
+__device__ __forceinline__ float sp_quad_left(float m3, float m1, float p1)
+{
+    return ((6.0f * m1 - m3) + 3.0f * p1) * 0.125f;
+}
+__device__ __forceinline__ float sp_quad_right(float m1, float p1, float p3)
+{
+    return ((3.0f * m1 + 6.0f * p1) - p3) * 0.125f;
+}
+// cubic with runtime coefficients: not-a-knot (9, 1, 1/16) or natural (23, 3, 1/40);
+// multiplying by 1 is exact, so the not-a-knot form is (9(m1+p1) - (m3+p3)) / 16.
+struct Cubic {
+    float a, b, c;
+};
+__device__ __forceinline__ Cubic cubic_coeffs(int natural)
+{
+    return natural ? Cubic{23.0f, 3.0f, 0.025f} : Cubic{9.0f, 1.0f, 0.0625f};
+}
+__device__ __forceinline__ float sp_cubic(const Cubic &k, float m3, float m1, float p1, float p3)
+{
+    return (k.a * (m1 + p1) - k.b * (m3 + p3)) * k.c;
+}
+
+// Level-wise quantization constants, read once per CTA from the header.
+struct LevelQ {
+    float e, twoe, inv2e;
+};
+
+// Quantize x against prediction p (Sec. III-A): q = rint((x - p) / 2e);
+// kept iff |q| < R and the reconstruction p + q*2e is within e of x.
+// Returns the code (q + R, or 0 for an outlier) and writes x' to xr.
+__device__ __forceinline__ uint32_t quantize(float x, float p, const LevelQ &L, int R, float Rf, float &xr)
+{
+    float d = x - p;
+    float v = d * L.inv2e;
+    float q = rintf(v);
+    bool ok = fabsf(q) < Rf;
+    int qi = ok ? (int)q : 0;
+    float r = p + (float)qi * L.twoe;
+    ok = ok && (fabsf(x - r) <= L.e);
+    xr = ok ? r : x;
+    return ok ? (uint32_t)(qi + R) : 0u;
+}
+
+__device__ __forceinline__ float dequantize(uint32_t code, float p, const LevelQ &L, int R, float outlier_value)
+{
+    return code ? p + (float)((int)code - R) * L.twoe : outlier_value;
+}
+
+}  // namespace gi
+
+// ------------------------------------------------------------- launchers
+// (C++ linkage, internal to the library; the C ABI lives in abi.cu)
+namespace gi {
+
+struct CompressArgs {
+    const float *x;
+    Dims dims;
+    float *anchors;
+    uint16_t *codes;
+    uint32_t *bitmap;
+    uint32_t *blockcnt;
+    uint32_t *hist;  // may be null
+    int radius;
+    const interp_header *hdr;
+    bool vec_x;      // x is 16-byte aligned and nx % 4 == 0: float4 row loads
+    bool vec_codes;  // codes are 16-byte aligned and nx % 8 == 0: 8-code row stores
+};
+
+struct DecompressArgs {
+    Dims dims;
+    const float *anchors;
+    const uint16_t *codes;
+    float *xrec;
+    const interp_header *hdr;
+    bool vec_codes;  // codes are 16-byte aligned and nx % 8 == 0
+    bool vec_xrec;   // xrec is 16-byte aligned and nx % 4 == 0
+};
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+cudaError_t launch_header_init(interp_header *hdr, Dims d, double eb, interp_config cfg, double alpha,
+                               cudaStream_t s);
+cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s);
+cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, double alpha, interp_header *hdr,
+                         void *partials, unsigned int *counter, int nblocks, cudaStream_t s);
+cudaError_t launch_compress_tiles(const CompressArgs &a, cudaStream_t s);
+cudaError_t launch_decompress_tiles(const DecompressArgs &a, cudaStream_t s);
+cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
+                                      const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
+                                      interp_header *hdr, cudaStream_t s);
+cudaError_t launch_outlier_scatter(const interp_header *hdr, const uint32_t *idx, const float *val,
+                                   uint64_t capacity, float *xrec, cudaStream_t s);
+cudaError_t launch_histogram(const uint16_t *codes, uint64_t n, int radius, uint32_t *hist, cudaStream_t s);
+
+int range_blocks();
+int sm_count();
+
+}  // namespace gi

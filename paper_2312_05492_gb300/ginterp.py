@@ -1,0 +1,332 @@
+"""Python binding of libginterp.so (include/ginterp.h).
+
+Argument marshalling only: torch supplies device memory and streams, every
+computation runs in the library's CUDA kernels.  The low-level functions keep
+the C names (interp_compress, interp_decompress, qcode_histogram,
+interp_autotune, ...) and take raw pointers; ``compress`` / ``decompress``
+wrap them for torch tensors.  There is no CPU fallback: if the library is
+missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libginterp.so")
+
+INTERP_OK, INTERP_EINVAL, INTERP_ECUDA, INTERP_EWORKSPACE, INTERP_ECAPACITY, INTERP_ENONFINITE = 0, -1, -2, -3, -4, -5
+STATUS_CAPACITY, STATUS_NONFINITE = 1, 2
+
+FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress", "interp_decompress",
+             "qcode_histogram", "interp_autotune", "interp_timing_enable", "interp_timing_read",
+             "interp_status_string")
+
+# kernels each call launches (memsets excluded): compress = [profile] + range or
+# header + tiles + outlier scan + outlier write; decompress = scatter + tiles
+def launches_compress(cfg: "Config") -> int:
+    return (1 if cfg.autotune else 0) + 1 + 1 + 2
+
+
+LAUNCHES_DECOMPRESS = 2
+
+
+class interp_config(ctypes.Structure):
+    _fields_ = [("dim_order", ctypes.c_int32 * 3), ("level_kind", ctypes.c_int32 * 3),
+                ("cubic_kind", ctypes.c_int32 * 3), ("eb_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("radius", ctypes.c_int32), ("alpha", ctypes.c_double)]
+
+
+class interp_header(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int64 * 3), ("cfg", interp_config), ("eb", ctypes.c_double),
+                ("eb_abs", ctypes.c_double), ("alpha", ctypes.c_double), ("e", ctypes.c_float * 3),
+                ("twoe", ctypes.c_float * 3), ("inv2e", ctypes.c_float * 3), ("vmin", ctypes.c_float),
+                ("vmax", ctypes.c_float), ("n_outliers", ctypes.c_uint64), ("n_nonfinite", ctypes.c_uint64),
+                ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("profile", ctypes.c_double * 18)]
+
+
+HEADER_BYTES = ctypes.sizeof(interp_header)
+_lib = None
+
+
+class InterpError(RuntimeError):
+    pass
+
+
+def load() -> ctypes.CDLL:
+    """Load libginterp.so (built by __graft_entry__.build() / build.py); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise InterpError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i64, u64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
+    dims_t = ctypes.POINTER(ctypes.c_int64)
+    cfg_p = ctypes.POINTER(interp_config)
+    lib.interp_anchor_count.restype = ctypes.c_size_t
+    lib.interp_anchor_count.argtypes = [dims_t]
+    lib.interp_workspace_bytes.restype = ctypes.c_size_t
+    lib.interp_workspace_bytes.argtypes = [dims_t, cfg_p]
+    lib.interp_compress.restype = ctypes.c_int
+    lib.interp_compress.argtypes = [P, dims_t, ctypes.c_double, cfg_p, P, P, P, P, u64, P, P, P, ctypes.c_size_t, P]
+    lib.interp_decompress.restype = ctypes.c_int
+    lib.interp_decompress.argtypes = [dims_t, P, P, P, P, P, u64, P, P]
+    lib.qcode_histogram.restype = ctypes.c_int
+    lib.qcode_histogram.argtypes = [P, u64, i32, P, P]
+    lib.interp_autotune.restype = ctypes.c_int
+    lib.interp_autotune.argtypes = [P, dims_t, cfg_p, P, P, ctypes.c_size_t, P]
+    lib.interp_timing_enable.restype = ctypes.c_int
+    lib.interp_timing_enable.argtypes = [ctypes.c_int]
+    lib.interp_timing_read.restype = ctypes.c_int
+    lib.interp_timing_read.argtypes = [P, P, P, P]
+    lib.interp_status_string.restype = ctypes.c_char_p
+    lib.interp_status_string.argtypes = [ctypes.c_int]
+    _lib = lib
+    return lib
+
+
+def _dims(dims) -> ctypes.Array:
+    return (ctypes.c_int64 * 3)(*[int(d) for d in dims])
+
+
+def _check(rc: int, what: str):
+    if rc != INTERP_OK:
+        msg = load().interp_status_string(rc).decode()
+        raise InterpError(f"{what} failed: {msg} ({rc})")
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# ----------------------------------------------------------- C-name entry points
+def interp_anchor_count(dims) -> int:
+    return int(load().interp_anchor_count(_dims(dims)))
+
+
+def interp_workspace_bytes(dims, cfg: interp_config) -> int:
+    return int(load().interp_workspace_bytes(_dims(dims), ctypes.byref(cfg)))
+
+
+def interp_compress(d_x, dims, eb, cfg, d_anchors, d_codes, d_out_idx, d_out_val, out_capacity, d_hist, d_hdr,
+                    d_ws, ws_bytes, stream) -> int:
+    return load().interp_compress(d_x, _dims(dims), float(eb), ctypes.byref(cfg), d_anchors, d_codes, d_out_idx,
+                                  d_out_val, int(out_capacity), d_hist, d_hdr, d_ws, int(ws_bytes), stream)
+
+
+def interp_decompress(dims, d_hdr, d_anchors, d_codes, d_out_idx, d_out_val, out_capacity, d_xrec, stream) -> int:
+    return load().interp_decompress(_dims(dims), d_hdr, d_anchors, d_codes, d_out_idx, d_out_val, int(out_capacity),
+                                    d_xrec, stream)
+
+
+def qcode_histogram(d_codes, n, radius, d_hist, stream) -> int:
+    return load().qcode_histogram(d_codes, int(n), int(radius), d_hist, stream)
+
+
+def interp_autotune(d_x, dims, cfg: interp_config, h_profile, d_ws, ws_bytes, stream) -> int:
+    return load().interp_autotune(d_x, _dims(dims), ctypes.byref(cfg), h_profile, d_ws, int(ws_bytes), stream)
+
+
+def interp_timing_enable(on: bool) -> int:
+    return load().interp_timing_enable(1 if on else 0)
+
+
+def interp_timing_read():
+    """(compress_ms, compress_launches, decompress_ms, decompress_launches) of the tile kernels."""
+    cm, dm = ctypes.c_double(), ctypes.c_double()
+    cn, dn = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().interp_timing_read(ctypes.byref(cm), ctypes.byref(cn), ctypes.byref(dm), ctypes.byref(dn)),
+           "interp_timing_read")
+    return cm.value, cn.value, dm.value, dn.value
+
+
+def interp_status_string(rc: int) -> str:
+    return load().interp_status_string(int(rc)).decode()
+
+
+# ---------------------------------------------------------------- torch API
+@dataclass
+class Config:
+    """Interpolation configuration (Sec. IV-B); mirrors interp_config.
+
+    level_kind is indexed by level l (stride 2**l): 0 = linear only, 1 = splines.
+    cubic_kind is indexed by axis (0=z, 1=y, 2=x): 0 = not-a-knot, 1 = natural.
+    """
+    dim_order: tuple = (0, 1, 2)
+    level_kind: tuple = (1, 1, 1)
+    cubic_kind: tuple = (0, 0, 0)
+    eb_mode: str = "rel"
+    autotune: bool = False
+    radius: int = 512
+    alpha: float = 0.0
+
+    def to_c(self) -> interp_config:
+        c = interp_config()
+        c.dim_order[:] = [int(v) for v in self.dim_order]
+        c.level_kind[:] = [int(v) for v in self.level_kind]
+        c.cubic_kind[:] = [int(v) for v in self.cubic_kind]
+        c.eb_mode = 1 if self.eb_mode == "rel" else 0
+        c.autotune = 1 if self.autotune else 0
+        c.radius = int(self.radius)
+        c.alpha = float(self.alpha)
+        return c
+
+
+@dataclass
+class CompressedField:
+    """Device-resident result of compress(): the header, anchors, quant-codes,
+    outlier list (capacity entries, the first n_outliers valid) and histogram."""
+    dims: tuple
+    cfg: Config
+    header: torch.Tensor      # uint8[HEADER_BYTES]
+    anchors: torch.Tensor     # float32
+    codes: torch.Tensor       # int16 storage of uint16 codes
+    out_idx: torch.Tensor     # int32 storage of uint32 indices
+    out_val: torch.Tensor     # float32
+    hist: torch.Tensor | None  # int32 storage of uint32 counts
+    capacity: int
+    _host_header: interp_header | None = field(default=None, repr=False)
+
+    def host_header(self, refresh: bool = False) -> interp_header:
+        """Copy the device header to the host (synchronises the current stream)."""
+        if self._host_header is None or refresh:
+            h = interp_header()
+            buf = self.header.cpu().numpy().tobytes()
+            ctypes.memmove(ctypes.addressof(h), buf, HEADER_BYTES)
+            self._host_header = h
+        return self._host_header
+
+    @property
+    def n_outliers(self) -> int:
+        return int(self.host_header().n_outliers)
+
+    @property
+    def status(self) -> int:
+        return int(self.host_header().status)
+
+    def nbytes(self) -> int:
+        n = min(self.n_outliers, self.capacity)
+        return HEADER_BYTES + self.anchors.numel() * 4 + self.codes.numel() * 2 + n * 8
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _check_field(x: torch.Tensor):
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.float32 or x.dim() != 3 or not x.is_cuda:
+        raise InterpError("expected a float32 3-D CUDA tensor")
+    if not x.is_contiguous():
+        raise InterpError("expected a contiguous tensor")
+
+
+class Workspace:
+    """Reusable device scratch for compress(); grows on demand."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.buf: torch.Tensor | None = None
+
+    def get(self, nbytes: int, device) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+        return self.buf
+
+
+_default_ws: dict = {}
+
+
+def default_capacity(n: int) -> int:
+    """Initial outlier capacity: N/64 entries (grown on overflow by compress)."""
+    return max(1024, n // 64)
+
+
+def allocate(dims, cfg: Config, device, capacity: int | None = None, hist: bool = True):
+    n = int(dims[0]) * int(dims[1]) * int(dims[2])
+    cap = default_capacity(n) if capacity is None else int(capacity)
+    return dict(
+        header=torch.zeros(HEADER_BYTES, dtype=torch.uint8, device=device),
+        anchors=torch.empty(interp_anchor_count(dims), dtype=torch.float32, device=device),
+        codes=torch.empty(n, dtype=torch.int16, device=device),
+        out_idx=torch.empty(max(cap, 1), dtype=torch.int32, device=device),
+        out_val=torch.empty(max(cap, 1), dtype=torch.float32, device=device),
+        hist=torch.empty(2 * int(cfg.radius), dtype=torch.int32, device=device) if hist else None,
+        capacity=cap,
+    )
+
+
+def compress_into(x: torch.Tensor, eb: float, cfg: Config, bufs: dict, ws: torch.Tensor, stream=None) -> None:
+    """Enqueue interp_compress on preallocated buffers (no synchronisation)."""
+    dims = tuple(x.shape)
+    rc = interp_compress(_ptr(x), dims, eb, cfg.to_c(), _ptr(bufs["anchors"]), _ptr(bufs["codes"]),
+                         _ptr(bufs["out_idx"]), _ptr(bufs["out_val"]), bufs["capacity"], _ptr(bufs["hist"]),
+                         _ptr(bufs["header"]), _ptr(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "interp_compress")
+
+
+def decompress_into(cf: CompressedField, out: torch.Tensor, stream=None) -> None:
+    rc = interp_decompress(cf.dims, _ptr(cf.header), _ptr(cf.anchors), _ptr(cf.codes), _ptr(cf.out_idx),
+                           _ptr(cf.out_val), cf.capacity, _ptr(out), _stream_ptr(stream))
+    _check(rc, "interp_decompress")
+
+
+def compress(x: torch.Tensor, eb: float, cfg: Config | None = None, capacity: int | None = None,
+             hist: bool = True, workspace: Workspace | None = None, stream=None,
+             grow_on_overflow: bool = True) -> CompressedField:
+    """Compress a float32 CUDA field.  With grow_on_overflow the call checks the
+    outlier count (one device-to-host read) and recompresses with a larger
+    outlier buffer if the first capacity was too small."""
+    _check_field(x)
+    cfg = cfg or Config()
+    dims = tuple(int(d) for d in x.shape)
+    ccfg = cfg.to_c()
+    wsb = interp_workspace_bytes(dims, ccfg)
+    if wsb == 0:
+        raise InterpError("invalid dims or configuration")
+    ws_obj = workspace or _default_ws.setdefault(x.device, Workspace())
+    ws = ws_obj.get(wsb, x.device)
+    bufs = allocate(dims, cfg, x.device, capacity, hist)
+    compress_into(x, eb, cfg, bufs, ws, stream)
+    cf = CompressedField(dims, cfg, bufs["header"], bufs["anchors"], bufs["codes"], bufs["out_idx"],
+                         bufs["out_val"], bufs["hist"], bufs["capacity"])
+    if grow_on_overflow:
+        h = cf.host_header(refresh=True)
+        if h.status & STATUS_CAPACITY:
+            return compress(x, eb, cfg, capacity=int(h.n_outliers), hist=hist, workspace=ws_obj, stream=stream,
+                            grow_on_overflow=False)
+    return cf
+
+
+def decompress(cf: CompressedField, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(cf.dims, dtype=torch.float32, device=cf.codes.device)
+    decompress_into(cf, out, stream)
+    return out
+
+
+def histogram(codes: torch.Tensor, radius: int, stream=None) -> torch.Tensor:
+    hist = torch.empty(2 * int(radius), dtype=torch.int32, device=codes.device)
+    rc = qcode_histogram(_ptr(codes), codes.numel(), radius, _ptr(hist), _stream_ptr(stream))
+    _check(rc, "qcode_histogram")
+    return hist
+
+
+def autotune(x: torch.Tensor, radius: int = 512, stream=None):
+    """Sampling profile + decision on the device; returns (Config, profile sums)."""
+    _check_field(x)
+    c = interp_config()
+    c.radius = radius
+    prof = (ctypes.c_double * 18)()
+    ws = torch.empty(HEADER_BYTES, dtype=torch.uint8, device=x.device)
+    rc = interp_autotune(_ptr(x), tuple(x.shape), c, ctypes.addressof(prof), _ptr(ws), ws.numel(),
+                         _stream_ptr(stream))
+    _check(rc, "interp_autotune")
+    cfg = Config(dim_order=tuple(c.dim_order), level_kind=tuple(c.level_kind), cubic_kind=tuple(c.cubic_kind),
+                 radius=radius)
+    return cfg, [float(v) for v in prof]

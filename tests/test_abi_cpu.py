@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI (no GPU needed): the shared library loads,
+exports every function declared in include/ginterp.h, its struct layouts match
+the binding, and argument errors are rejected before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2312_05492_gb300 import build, ginterp
+    build.build()
+    return ginterp
+
+
+def _declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            if m.group(1) not in ("if", "while", "for", "sizeof", "return"):
+                names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("interp_compress", "interp_decompress", "qcode_histogram", "interp_autotune"):
+        assert required in names
+
+
+def test_library_exports_every_declared_function(G):
+    lib = ctypes.CDLL(G.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert set(G.FUNCTIONS) <= set(_declared_functions())
+
+
+def test_struct_layouts(G):
+    assert ctypes.sizeof(G.interp_config) == 56
+    assert ctypes.sizeof(G.interp_header) == 320
+    assert G.interp_header.profile.offset == 176
+
+
+def test_anchor_count_and_workspace(G):
+    assert G.interp_anchor_count((64, 64, 64)) == 512
+    assert G.interp_anchor_count((449, 449, 235)) == 57 * 57 * 30
+    assert G.interp_anchor_count((0, 4, 4)) == 0
+    cfg = G.Config().to_c()
+    ws = G.interp_workspace_bytes((512, 512, 512), cfg)
+    assert ws >= 512 * 512 * 16 * 4  # one bitmap word per 32 x-positions
+    bad = G.Config(dim_order=(0, 0, 1)).to_c()
+    assert G.interp_workspace_bytes((8, 8, 8), bad) == 0
+    assert G.interp_workspace_bytes((1 << 11, 1 << 11, 1 << 11), cfg) == 0  # N >= 2^32
+
+
+@pytest.mark.parametrize("change", [
+    dict(radius=1), dict(radius=40000), dict(dim_order=(0, 1, 1)), dict(level_kind=(2, 1, 1)),
+    dict(cubic_kind=(0, 3, 0)),
+])
+def test_compress_rejects_bad_config(G, change):
+    cfg = G.Config(**change).to_c()
+    rc = G.interp_compress(1, (8, 8, 8), 1e-3, cfg, 1, 1, 1, 1, 16, None, 1, 1, 1 << 20, None)
+    assert rc == G.INTERP_EINVAL
+
+
+def test_compress_rejects_bad_arguments(G):
+    cfg = G.Config().to_c()
+    ok = dict(d_x=1, dims=(8, 8, 8), eb=1e-3)
+    assert G.interp_compress(1, (8, 8, 8), 0.0, cfg, 1, 1, 1, 1, 16, None, 1, 1, 1 << 20, None) == G.INTERP_EINVAL
+    assert G.interp_compress(1, (8, 8, 8), float("nan"), cfg, 1, 1, 1, 1, 16, None, 1, 1, 1 << 20,
+                             None) == G.INTERP_EINVAL
+    assert G.interp_compress(None, (8, 8, 8), 1e-3, cfg, 1, 1, 1, 1, 16, None, 1, 1, 1 << 20,
+                             None) == G.INTERP_EINVAL
+    assert G.interp_compress(1, (8, 0, 8), 1e-3, cfg, 1, 1, 1, 1, 16, None, 1, 1, 1 << 20, None) == G.INTERP_EINVAL
+    assert G.interp_compress(1, (8, 8, 8), 1e-3, cfg, 1, 1, None, 1, 16, None, 1, 1, 1 << 20,
+                             None) == G.INTERP_EINVAL
+    assert G.interp_compress(1, (8, 8, 8), 1e-3, cfg, 1, 1, 1, 1, 16, None, 1, 1, 16, None) == G.INTERP_EWORKSPACE
+    assert ok  # argument errors above never reached CUDA
+    assert G.qcode_histogram(1, 10, 1, 1, None) == G.INTERP_EINVAL
+    assert G.interp_decompress((8, 8, 8), None, 1, 1, 1, 1, 4, 1, None) == G.INTERP_EINVAL
+    assert G.interp_status_string(G.INTERP_EWORKSPACE) == "workspace too small"
+
+
+def test_binding_refuses_cpu_tensors(G):
+    import torch
+    with pytest.raises(G.InterpError):
+        G.compress(torch.zeros(8, 8, 8), 1e-3)

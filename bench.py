@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark: G-Interp compress + decompress round trip on one GB300 per rank.
+
+Workload: 512x512x512 float32 lognormal field (exp of a Gaussian random field
+with spectrum k^-11/3, seed 1), value-range-relative error bound 1e-3, spline
+levels with the dim order, cubic type per axis and linear/spline per level
+chosen by the on-device sampling autotuner.  One step = one pass of the whole
+hot path over the field: sampling profile + decision, value range + level
+bounds, fused predict-quantize with histogram and outlier bitmap, ordered
+outlier compaction, outlier scatter and reconstruction.
+
+value = field bytes (4 N) per step / device time per step (GB/s), summed over
+ranks (weak scaling: every rank compresses its own field).  The field (512
+MiB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+--impl reference times the CPU oracle (the plain restatement of the paper used
+by the tests) on a bounded slab of the same field instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress/decompress GB/s & % HBM roofline at rel eb 1e-3; served p50/p99 latency"
+SHAPE = (512, 512, 512)
+EB = 1e-3
+WORKLOAD = "512^3 float32 lognormal exp(GRF k^-11/3) seed 1, rel eb 1e-3, autotuned spline levels"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--eb", type=float, default=EB)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling runs only)")
+    a = p.parse_args()
+    a.shape = tuple(int(v) for v in a.shape.split(",")) if a.shape else SHAPE
+    return a
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2312_05492_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("source_hash") != source_hash():
+            return None
+        return d["kernels"][kernel]["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2312_05492_gb300 import fields
+    from paper_2312_05492_gb300 import ginterp as G
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    G.load()
+    x = fields.lognormal(args.shape, 11.0 / 3.0, 1 + 1000 * rank, device=dev)
+    torch.cuda.empty_cache()  # release the FFT temporaries of the generator
+    n = x.numel()
+    nbytes = 4 * n
+    cfg = G.Config(autotune=True, eb_mode="rel", level_kind=(1, 1, 1), radius=512)
+    dims = tuple(x.shape)
+    ws = torch.empty(G.interp_workspace_bytes(dims, cfg.to_c()), dtype=torch.uint8, device=dev)
+    bufs = G.allocate(dims, cfg, dev, capacity=n // 64)
+    cf = G.CompressedField(dims, cfg, bufs["header"], bufs["anchors"], bufs["codes"], bufs["out_idx"],
+                           bufs["out_val"], bufs["hist"], bufs["capacity"])
+    xrec = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        G.compress_into(x, args.eb, cfg, bufs, ws, stream)
+        G.decompress_into(cf, xrec, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    h = cf.host_header(refresh=True)
+    assert h.status & G.STATUS_CAPACITY == 0, "outlier capacity exceeded"
+    err = float((xrec - x).abs().max())
+    assert err <= h.eb_abs, (err, h.eb_abs)
+
+    # ---- timed region: K round trips
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    G.interp_timing_enable(True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    G.interp_timing_enable(False)
+    barrier()
+    clocks = sampler.stop()
+    ms_total = t0.elapsed_time(t1)
+    cms, cn, dms, dn = G.interp_timing_read()
+    ms_step = ms_total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+
+    # ---- compress-only and decompress-only throughput (same buffers)
+    def timed(fn, k):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    ms_c = timed(lambda: G.compress_into(x, args.eb, cfg, bufs, ws, stream), max(args.steps, 5))
+    ms_d = timed(lambda: G.decompress_into(cf, xrec, stream), max(args.steps, 5))
+
+    h = cf.host_header(refresh=True)
+    n_out = int(h.n_outliers)
+    A = G.interp_anchor_count(dims)
+    peak, peak_kind = measured_peaks()
+    comp_tile_ms = cms / max(cn, 1)
+    dec_tile_ms = dms / max(dn, 1)
+    comp_alg = 6 * n + 4 * A                      # x read, codes write, anchors write
+    dec_alg = 6 * n + 4 * A + 4 * n_out           # codes read, anchors read, outlier values, field write
+    step_alg = (10 * n + 4 * A + 8 * n_out + 8 * 512) + (6 * n + 4 * A + 8 * n_out)
+    achieved = comp_alg / (comp_tile_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_compress (fused predict-quantize tile kernel)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": ncu_traffic("k_compress"), "algorithmic_bytes_per_launch": comp_alg,
+                "avg_launch_ms": round(comp_tile_ms, 5), "launches_timed": cn}
+    dec_ach = dec_alg / (dec_tile_ms * 1e-3) / 1e9
+    roofline_dec = {"bound": "hbm", "kernel": "k_decompress", "achieved": round(dec_ach, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(dec_ach / peak, 4), "traffic": ncu_traffic("k_decompress"),
+                    "algorithmic_bytes_per_launch": dec_alg, "avg_launch_ms": round(dec_tile_ms, 5)}
+    step_gbs = step_alg / (ms_step * 1e-3) / 1e9
+
+    value = world * nbytes / (ms_step * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.shape == SHAPE else f"profiling case {args.shape}",
+                   "shape": list(args.shape), "eb_rel": args.eb, "eb_abs": h.eb_abs,
+                   "alpha": h.alpha, "dim_order": list(h.cfg.dim_order), "level_kind": list(h.cfg.level_kind),
+                   "cubic_kind": list(h.cfg.cubic_kind), "radius": 512, "n_outliers": n_out,
+                   "l2_flush": "not needed: inputs (512 MiB field) exceed the 129 MB L2",
+                   "parallelism": f"replicas x{world} (independent fields)"},
+        "compress_gbs": round(nbytes / (ms_c * 1e-3) / 1e9, 2),
+        "decompress_gbs": round(nbytes / (ms_d * 1e-3) / 1e9, 2),
+        "compress_ms": round(ms_c, 4), "decompress_ms": round(ms_d, 4),
+        "roofline": roofline, "roofline_decompress": roofline_dec,
+        "roofline_step": {"bound": "hbm", "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
+                          "frac": round(step_gbs / peak, 4), "algorithmic_bytes_per_step": step_alg},
+        "max_abs_err_over_eb": err / h.eb_abs,
+        "gpu_launches": (G.launches_compress(cfg) + G.LAUNCHES_DECOMPRESS) * args.steps,
+        "clocks": clocks,
+    }
+
+    # ---- end to end through the public API with host buffers
+    if not args.no_e2e:
+        host_x = torch.empty(dims, dtype=torch.float32, pin_memory=True)
+        host_x.copy_(x.cpu())
+        host_out = torch.empty(dims, dtype=torch.float32, pin_memory=True)
+        xd = torch.empty_like(x)
+
+        def e2e_step():
+            xd.copy_(host_x, non_blocking=True)
+            G.compress_into(xd, args.eb, cfg, bufs, ws, stream)
+            G.decompress_into(cf, xrec, stream)
+            host_out.copy_(xrec, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        k = max(3, min(args.steps, 10))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        barrier()
+        a.record(stream)
+        for _ in range(k):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / k
+        out["e2e"] = {"value": round(world * nbytes / (e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+                      "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": round(e_ms, 4),
+                      "what": "pinned host field -> compress -> decompress -> pinned host reconstruction"}
+        assert torch.equal(host_out.view(torch.int32), xrec.cpu().view(torch.int32))
+
+    # ---- CPU baseline: the oracle as it stands, single-threaded, rank 0 only
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(x, args.eb, full=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(x_t, eb, full: bool, planes: int = 64):
+    """Time the oracle round trip (profile + decision, range, compress,
+    decompress) on the host.  full=True: the whole field; else a z-slab."""
+    import numpy as np
+
+    import oracle as O
+    xs = x_t[:planes] if not full else x_t
+    x = np.ascontiguousarray(xs.cpu().numpy())
+    t = time.perf_counter()
+    cfg = O.autotune(x)
+    eb_abs, e, twoe, inv2e = O.bounds_for(x, eb, "rel")
+    c = O.compress(x, cfg, e, twoe, inv2e, eb_abs)
+    O.decompress(c)
+    dt = time.perf_counter() - t
+    return {"value": round(x.nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "seconds": round(dt, 3),
+            "sample": f"{'full field' if full else f'z-slab {x.shape}'} {x.shape}, one round trip "
+                      f"(autotune, range, compress, decompress), single thread"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import torch
+
+    from paper_2312_05492_gb300 import fields
+    planes = 64
+    x = fields.lognormal(SHAPE, 11.0 / 3.0, 1, device="cuda" if torch.cuda.is_available() else "cpu")
+    xs = x[:planes].cpu()
+    nbytes = xs.numel() * 4
+    for _ in range(args.warmup):
+        cpu_baseline(xs, args.eb, full=True)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_baseline(xs, args.eb, full=True)
+    dt = (time.perf_counter() - t) / max(args.steps, 1)
+    value = nbytes / dt / 1e9
+    cb = {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+          "sample": f"z-slab {tuple(xs.shape)} of the 512^3 lognormal field per step, one round trip, single thread"}
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "shape": list(SHAPE), "eb_rel": args.eb},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

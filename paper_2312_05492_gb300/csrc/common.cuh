@@ -19,12 +19,21 @@ namespace gi {
 // staged in shared memory together with the closing faces at the far end of
 // each axis (the "borrowed" anchors and face points of the neighbouring
 // chunks, Sec. IV-C), i.e. a (8TZ+1) x (8TY+1) x (8TX+1) box.
-constexpr int TZ = 2, TY = 2, TX = 4;
+#ifndef GI_TILE_Z
+#define GI_TILE_Z 2
+#endif
+#ifndef GI_TILE_Y
+#define GI_TILE_Y 2
+#endif
+#ifndef GI_TILE_THREADS
+#define GI_TILE_THREADS 256
+#endif
+constexpr int TZ = GI_TILE_Z, TY = GI_TILE_Y, TX = 4;
 constexpr int OZ = 8 * TZ, OY = 8 * TY, OX = 8 * TX;  // owned extent
 constexpr int BZ = OZ + 1, BY = OY + 1, BX = OX + 1;  // box extent (with far faces)
 constexpr int BOX = BZ * BY * BX;
 constexpr int OWN = OZ * OY * OX;
-constexpr int TILE_THREADS = 256;
+constexpr int TILE_THREADS = GI_TILE_THREADS;
 static_assert(OX == 32, "one outlier-bitmap word covers the 32 x-positions of an owned row");
 
 // outlier bitmap: one 32-bit word per 32 x-positions of every (z, y) row

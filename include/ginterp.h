@@ -51,6 +51,8 @@ typedef enum {
 /* device-side status bits (interp_header.status) */
 #define INTERP_STATUS_CAPACITY 1u  /* more outliers than out_capacity; n_outliers is the true count */
 #define INTERP_STATUS_NONFINITE 2u /* the field holds NaN/Inf (stored losslessly as outliers) */
+#define INTERP_STATUS_TIMEOUT 4u   /* a tile kernel gave up waiting for an input transfer (its
+                                      output is incomplete); set by compression and decompression */
 
 /* Interpolation configuration (Sec. IV-B). */
 typedef struct {

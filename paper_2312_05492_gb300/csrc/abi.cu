@@ -47,6 +47,11 @@ bool cfg_ok(const interp_config *c)
     return true;
 }
 
+// outlier bitmap: one word per 32 x-positions of every row; the counters are
+// per 2048 words in ascending index order, the words themselves are stored
+// tile-major (see tiles.cu)
+Dims to_dims(const int64_t *d) { return Dims{(int)d[0], (int)d[1], (int)d[2]}; }
+
 int64_t bitmap_words(const int64_t *dims) { return dims[0] * dims[1] * ((dims[2] + 31) / 32); }
 
 struct WsLayout {
@@ -63,7 +68,7 @@ WsLayout ws_layout(const int64_t *dims)
     L.ctrl = 0;
     L.partials = kCtrlBytes;
     L.bitmap = align_up(L.partials + gi::range_partials_bytes());
-    L.blockcnt = align_up(L.bitmap + sizeof(uint32_t) * (size_t)L.words);
+    L.blockcnt = align_up(L.bitmap + sizeof(uint32_t) * gi::bitmap_words_tiled(to_dims(dims)));
     L.total = align_up(L.blockcnt + sizeof(uint32_t) * (size_t)L.nblk);
     return L;
 }
@@ -84,8 +89,6 @@ double effective_alpha(const interp_config &c, double eb)
     if (c.alpha > 0) return c.alpha;
     return c.eb_mode ? alpha_of_eps(eb) : 1.0;
 }
-
-Dims to_dims(const int64_t *d) { return Dims{(int)d[0], (int)d[1], (int)d[2]}; }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? INTERP_OK : INTERP_ECUDA; }
 
@@ -159,7 +162,7 @@ int interp_compress(const float *d_x, const int64_t dims[3], double eb, const in
     }
     if (e == cudaSuccess) {
         gi::CompressArgs a{d_x, d, d_anchors, d_codes, bitmap, blockcnt, d_hist, c.radius, d_hdr,
-                           gi::aligned16(d_x) && d.nx % 4 == 0, gi::aligned16(d_codes) && d.nx % 8 == 0};
+                           gi::aligned16(d_codes) && d.nx % 8 == 0};
         timing_mark(0, 0, s);
         e = gi::launch_compress_tiles(a, s);
         timing_mark(0, 1, s);
@@ -182,8 +185,7 @@ int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const f
     cudaError_t e = cudaSuccess;
     if (out_capacity > 0) e = gi::launch_outlier_scatter(d_hdr, d_out_idx, d_out_val, out_capacity, d_xrec, s);
     if (e == cudaSuccess) {
-        gi::DecompressArgs a{d, d_anchors, d_codes, d_xrec, d_hdr, gi::aligned16(d_codes) && d.nx % 8 == 0,
-                             gi::aligned16(d_xrec) && d.nx % 4 == 0};
+        gi::DecompressArgs a{d, d_anchors, d_codes, d_xrec, d_hdr, gi::aligned16(d_xrec) && d.nx % 4 == 0};
         timing_mark(1, 0, s);
         e = gi::launch_decompress_tiles(a, s);
         timing_mark(1, 1, s);

@@ -19,20 +19,12 @@ namespace gi {
 // staged in shared memory together with the closing faces at the far end of
 // each axis (the "borrowed" anchors and face points of the neighbouring
 // chunks, Sec. IV-C), i.e. a (8TZ+1) x (8TY+1) x (8TX+1) box.
-#ifndef GI_TILE_Z
-#define GI_TILE_Z 2
-#endif
-#ifndef GI_TILE_Y
-#define GI_TILE_Y 2
-#endif
+// A CTA marches along z through a column of 2 x 4 chunks of 8^3 points
+// (16 y x 32 x owned points), one slab of 8 planes at a time.
 #ifndef GI_TILE_THREADS
 #define GI_TILE_THREADS 256
 #endif
-constexpr int TZ = GI_TILE_Z, TY = GI_TILE_Y, TX = 4;
-constexpr int OZ = 8 * TZ, OY = 8 * TY, OX = 8 * TX;  // owned extent
-constexpr int BZ = OZ + 1, BY = OY + 1, BX = OX + 1;  // box extent (with far faces)
-constexpr int BOX = BZ * BY * BX;
-constexpr int OWN = OZ * OY * OX;
+constexpr int OY = 16, OX = 32;  // owned extent of a column
 constexpr int TILE_THREADS = GI_TILE_THREADS;
 static_assert(OX == 32, "one outlier-bitmap word covers the 32 x-positions of an owned row");
 
@@ -118,9 +110,8 @@ struct CompressArgs {
     uint32_t *blockcnt;
     uint32_t *hist;  // may be null
     int radius;
-    const interp_header *hdr;
-    bool vec_x;      // x is 16-byte aligned and nx % 4 == 0: float4 row loads
-    bool vec_codes;  // codes are 16-byte aligned and nx % 8 == 0: 8-code row stores
+    interp_header *hdr;
+    bool vec_codes;  // codes 16-byte aligned and nx % 8 == 0: 8-code vector stores
 };
 
 struct DecompressArgs {
@@ -129,8 +120,7 @@ struct DecompressArgs {
     const uint16_t *codes;
     float *xrec;
     const interp_header *hdr;
-    bool vec_codes;  // codes are 16-byte aligned and nx % 8 == 0
-    bool vec_xrec;   // xrec is 16-byte aligned and nx % 4 == 0
+    bool vec_xrec;  // xrec 16-byte aligned and nx % 4 == 0: 4-value vector stores
 };
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -142,6 +132,7 @@ cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, d
                          void *partials, unsigned int *counter, int nblocks, cudaStream_t s);
 cudaError_t launch_compress_tiles(const CompressArgs &a, cudaStream_t s);
 cudaError_t launch_decompress_tiles(const DecompressArgs &a, cudaStream_t s);
+size_t bitmap_words_tiled(Dims d);
 cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
                                       const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
                                       interp_header *hdr, cudaStream_t s);

@@ -61,11 +61,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_outlier_scan(uint32_t *blockcn
     }
 }
 
+// Word gw (ascending index order: row = gw / words_per_row, 32 x-positions
+// each) lives at a tile-major address: the compression tiles own 16 rows x 32
+// columns and write their words contiguously per plane.
+__device__ __forceinline__ size_t tiled_word(long long gw, int words_per_row, int ny, int nz)
+{
+    const long long row = gw / words_per_row;
+    const int cx = (int)(gw - row * words_per_row);
+    const int gz = (int)(row / ny), gy = (int)(row - (long long)gz * ny);
+    const size_t col = (size_t)(gy / 16) * words_per_row + cx;
+    return (col * nz + gz) * 16 + (gy % 16);
+}
+
 __global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const uint32_t *__restrict__ bitmap,
                                                                  const uint32_t *__restrict__ offsets,
-                                                                 long long words, int words_per_row, int nx,
-                                                                 const float *__restrict__ x, uint32_t *out_idx,
-                                                                 float *out_val, unsigned long long capacity,
+                                                                 long long words, int words_per_row, int nx, int ny,
+                                                                 int nz, const float *__restrict__ x,
+                                                                 uint32_t *out_idx, float *out_val,
+                                                                 unsigned long long capacity,
                                                                  const interp_header *hdr, int nblk)
 {
     const int b = blockIdx.x;
@@ -79,7 +92,7 @@ __global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const uint32_t 
     int cnt = 0;
 #pragma unroll
     for (int k = 0; k < WORDS_PER_THREAD; ++k) {
-        wv[k] = (w0 + k < words) ? bitmap[w0 + k] : 0u;
+        wv[k] = (w0 + k < words) ? bitmap[tiled_word(w0 + k, words_per_row, ny, nz)] : 0u;
         cnt += __popc(wv[k]);
     }
     // block exclusive scan of per-thread counts
@@ -196,8 +209,8 @@ cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int words_per_row = (d.nx + 31) / 32;
-    k_outlier_write<<<nblk, WRITE_THREADS, 0, s>>>(bitmap, blockcnt, (long long)words, words_per_row, d.nx, x,
-                                                  out_idx, out_val, (unsigned long long)capacity, hdr, nblk);
+    k_outlier_write<<<nblk, WRITE_THREADS, 0, s>>>(bitmap, blockcnt, (long long)words, words_per_row, d.nx, d.ny,
+                                                  d.nz, x, out_idx, out_val, (unsigned long long)capacity, hdr, nblk);
     return cudaGetLastError();
 }
 

@@ -1,133 +1,230 @@
 // G-Interp tile kernels: fused predict-quantize (compression) and the
 // reconstruction replay (decompression), Sec. IV-A/B/C of arXiv 2312.05492.
 //
-// One CTA owns a tile of TZ x TY x TX chunks of 8^3 points.  Because every
-// interpolation stays inside the closed 8^3 chunk along its axis (anchors
-// "bound" the interpolation, Sec. IV-A), a tile depends only on the original
-// values of its box = owned points + the closing faces at the far end of
-// each axis.  The CTA stages that box in shared memory, recomputes the
-// far-face points (bit-identical to what the neighbouring tile computes for
-// them), and runs the nine dependent passes (strides 4, 2, 1; three axes
-// each, Sec. IV-A) with a barrier between passes.
+// Decomposition.  Every interpolation stays inside the closed 8^3 chunk along
+// its axis (anchors bound it, Sec. IV-A), so a column of 2 x 4 chunks
+// (16 y x 32 x owned points) can be processed one 8-plane slab at a time: the
+// slab's box is 9 planes x 17 rows x 33 columns (owned points plus the
+// closing faces at the far end of each axis).  The face plane shared by two
+// consecutive slabs depends only on values inside that plane, so it is
+// computed once and carried to the next slab; the far row (y) and column (x)
+// faces are recomputed by the neighbouring column (bit-identical values).
 //
-// Work unit inside a pass: one chunk segment, i.e. the 9 points of one line
-// along the pass axis inside one chunk.  Its known points (even multiples of
-// s) give every prediction of the segment (1, 2 or 4 of them) from registers:
-// the full-chunk stencils are fixed (Fig. 3); chunks truncated by the field's
-// far edge take the neighbour-count rule point by point.
-#include "common.cuh"
+// Persistent CTAs take work items = (column, run of slabs) round-robin and
+// march along z.  One thread issues a TMA box load of the next slab into a
+// dense staging buffer while the CTA runs the nine dependent passes (strides
+// 4, 2, 1; three axes each, a barrier between passes) on the current slab;
+// the staging buffer is then repacked into the compute box, whose odd row
+// pitch (33 floats) and plane pitch (561) make row-per-thread and
+// column-per-thread walks free of shared-memory bank conflicts.
+//
+// Work unit inside a pass: one chunk segment, i.e. the 9 points of a line
+// along the pass axis inside one chunk; its known points (even multiples of
+// s) give all 1, 2 or 4 predictions of the segment from registers.
+// Full-chunk stencils are fixed (Fig. 3); chunks truncated by the field's far
+// edge take the neighbour-count rule point by point.
+#include <cstring>
+
+#include "tma.cuh"
 
 namespace gi {
 namespace {
 
-__host__ __device__ constexpr int box_ext(int a) { return a == 2 ? BX : (a == 1 ? BY : BZ); }
-__host__ __device__ constexpr int own_ext(int a) { return a == 2 ? OX : (a == 1 ? OY : OZ); }
-__host__ __device__ constexpr int box_stride(int a) { return a == 2 ? 1 : (a == 1 ? BX : BX * BY); }
-__host__ __device__ constexpr int own_stride(int a) { return a == 2 ? 1 : (a == 1 ? OX : OX * OY); }
-__host__ __device__ constexpr int chunks_of(int a) { return a == 2 ? TX : (a == 1 ? TY : TZ); }
-// the two axes other than d: U is the faster-varying one in memory
-__host__ __device__ constexpr int axis_u(int d) { return d == 2 ? 1 : 2; }
+// ------------------------------------------------------------ geometry
+constexpr int NT = TILE_THREADS;
+constexpr int NWARP = NT / 32;
+constexpr int EZ = 9, EY = OY + 1, EX = OX + 1;  // slab box extents (z, y, x)
+constexpr int PLANE = EY * EX;                   // 561 floats, odd: conflict-free row walks
+constexpr int BOXF = EZ * PLANE;                 // floats per slab box
+constexpr int CP = OX + 2;                       // u16 pitch of code rows (17 words, odd)
+constexpr int STAGE_PLANE = OY * CP;             // compression code staging: owned rows only
+constexpr int STAGE = EZ * STAGE_PLANE;
+constexpr int CBOX_PLANE = EY * CP;              // decompression code box: all rows
+constexpr int CBOX = EZ * CBOX_PLANE;
+// TMA landing buffers: dense boxes whose rows are a multiple of 16 bytes
+constexpr int XP = 36;                           // floats per landed row (x 0..35)
+constexpr int XLAND = EZ * EY * XP;
+constexpr int KP = 40;                           // codes per landed row (x 0..39)
+constexpr int KLAND = EZ * EY * KP;
+constexpr uint32_t kTmaPolls = 1u << 22;         // bounded wait for one TMA box
+
+__host__ __device__ constexpr int ext_of(int a) { return a == 2 ? EX : (a == 1 ? EY : EZ); }
+__host__ __device__ constexpr int own_of(int a) { return a == 2 ? OX : (a == 1 ? OY : EZ); }
+__host__ __device__ constexpr int bstride(int a) { return a == 2 ? 1 : (a == 1 ? EX : PLANE); }
+__host__ __device__ constexpr int sstride(int a) { return a == 2 ? 1 : (a == 1 ? CP : STAGE_PLANE); }
+__host__ __device__ constexpr int cstride(int a) { return a == 2 ? 1 : (a == 1 ? CP : CBOX_PLANE); }
+__host__ __device__ constexpr int chunks_of(int a) { return a == 2 ? OX / 8 : (a == 1 ? OY / 8 : 1); }
+__host__ __device__ constexpr int axis_u(int d) { return d == 2 ? 1 : 2; }  // faster other axis
 __host__ __device__ constexpr int axis_v(int d) { return d == 0 ? 1 : 0; }
-__host__ __device__ constexpr int rank_in(int a, int o0, int o1, int o2) { return a == o0 ? 0 : (a == o1 ? 1 : 2); }
+__host__ __device__ constexpr int count_on(int e, int step) { return (e - 1) / step + 1; }
+__host__ __device__ constexpr uint32_t magic_of(int n)
+{
+    return n <= 1 ? 0u : (uint32_t)((0x100000000ull + (unsigned long long)n - 1) / (unsigned long long)n);
+}
 
-// dynamic shared-memory layout; every sub-array starts on a 16-byte boundary
-__host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
-constexpr size_t kCompressCodesOff = align16(sizeof(float) * BOX);
-constexpr size_t kCompressHistOff = align16(kCompressCodesOff + sizeof(uint16_t) * OWN);
-constexpr size_t kCompressSmem = kCompressHistOff + sizeof(uint32_t) * HIST_SMEM_BINS;
-constexpr size_t kDecompressCodesOff = align16(sizeof(float) * BOX);
-constexpr size_t kDecompressSmem = kDecompressCodesOff + sizeof(uint16_t) * BOX;
-static_assert(kCompressCodesOff % 16 == 0 && (sizeof(uint16_t) * OX) % 16 == 0, "uint4 access to owned code rows");
+// floor(w / n) for 0 <= w < 2^16 and 1 <= n <= 64, given magic_of(n) (0 for n = 1)
+__device__ __forceinline__ int fdiv(int w, uint32_t m) { return m ? (int)__umulhi((uint32_t)w, m) : w; }
 
-struct TileCtx {
-    int g0[3];  // global origin of the tile (z, y, x)
-    int n[3];   // field dims
+// dynamic shared-memory layouts: the TMA landing buffer first (the dynamic
+// shared-memory base is 128-byte aligned), then 16-byte aligned sub-arrays
+__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) / 16 * 16; }
+constexpr size_t C_LAND = 0;
+constexpr size_t C_BOX = al16(C_LAND + sizeof(float) * XLAND);
+constexpr size_t C_STAGE = al16(C_BOX + sizeof(float) * BOXF);
+constexpr size_t C_HIST = al16(C_STAGE + sizeof(uint16_t) * STAGE);
+constexpr size_t C_BAR = al16(C_HIST + sizeof(uint32_t) * HIST_SMEM_BINS);
+constexpr size_t kCompressSmem = C_BAR + 16;
+constexpr size_t D_LAND = 0;
+constexpr size_t D_BOX = al16(D_LAND + sizeof(uint16_t) * KLAND);
+constexpr size_t D_CBOX = al16(D_BOX + sizeof(float) * BOXF);
+constexpr size_t D_BAR = al16(D_CBOX + sizeof(uint16_t) * CBOX);
+constexpr size_t kDecompressSmem = D_BAR + 16;
+// 4 compression CTAs per SM: dynamic + static (~128 B) + 1 KB reserved each, in 228 KB
+static_assert(4 * (kCompressSmem + 128 + 1024) <= 228 * 1024, "four compression CTAs per SM");
+
+// ------------------------------------------------------------ cp.async (fallback path)
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ------------------------------------------------------------ context
+struct Field {
+    int n[3];    // nz, ny, nx
+    int cols_x;  // columns along x
+    int cols;    // columns in total
+    int slabs;   // slabs along z
+    int run;     // slabs per work item
+    int items;   // work items
+};
+
+struct Slab {
+    int g0[3];           // global origin of the slab box (z, y, x)
+    int col;             // column index (cy * cols_x + cx)
+    bool carried;        // plane 0 carried from the previous slab (not recomputed)
+    int own_lo, own_hi;  // local planes whose outputs this slab writes
+};
+
+// Per-call constants, one copy in shared memory.
+struct Levels {
     LevelQ L[3];
+    int spline[3];
+    Cubic cub[3];
+    int order[3];
+    int rank[3];  // position of each axis in the order
     int R;
     float Rf;
-    int spline[3];  // per level
-    Cubic cub[3];   // per axis
 };
 
-struct CompressSink {
-    uint16_t *own_codes;  // [OZ][OY][OX]
-    uint32_t *hist_s;     // shared bins or null
-    uint32_t *hist_g;     // global bins (used when hist_s is null); may be null
-    uint32_t central;     // register count of code R
+__device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
+{
+    for (int l = 0; l < 3; ++l) {
+        lv.L[l].e = h->e[l];
+        lv.L[l].twoe = h->twoe[l];
+        lv.L[l].inv2e = h->inv2e[l];
+        lv.spline[l] = h->cfg.level_kind[l];
+        lv.cub[l] = cubic_coeffs(h->cfg.cubic_kind[l]);
+        lv.order[l] = h->cfg.dim_order[l];
+    }
+    for (int k = 0; k < 3; ++k) lv.rank[lv.order[k]] = k;
+    lv.R = h->cfg.radius;
+    lv.Rf = (float)lv.R;
+}
+
+// Slab c of an item covers planes [8c, 8c+8].  It writes the outputs of
+// planes [8c, 8c+8] except: plane 8c when carried (the previous slab of the
+// run wrote it as its plane 8), and plane 8c+8 when the run ends there and it
+// is not the field's last plane (the next run starts with it).
+__device__ __forceinline__ void slab_setup(Slab &s, const Field &f, int item, int c, int c_first, int c_last)
+{
+    const int col = item % f.cols;
+    const int cx = col % f.cols_x, cy = col / f.cols_x;
+    s.g0[0] = 8 * c;
+    s.g0[1] = OY * cy;
+    s.g0[2] = OX * cx;
+    s.col = col;
+    s.carried = c != c_first;
+    s.own_lo = s.carried ? 1 : 0;
+    const bool field_end = 8 * c + 8 == f.n[0] - 1;
+    s.own_hi = (c != c_last || field_end) ? 8 : 7;
+}
+
+// ------------------------------------------------------------ passes
+struct Sink {
+    uint16_t *stage;       // compression: code staging
+    const uint16_t *cbox;  // decompression: code box
 };
 
-// One pass (level S, axis D).  U_EARLY / V_EARLY: whether the other axes come
-// before D in the dim order (then they are on the s-grid, else on the 2s-grid).
-template <bool COMPRESS, int S, int D, bool U_EARLY, bool V_EARLY>
-__device__ __forceinline__ void run_pass(float *__restrict__ box, uint16_t *__restrict__ cbox, const TileCtx &c,
-                                         CompressSink &sink)
+template <bool COMPRESS, int S, int D>
+__device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk, const Slab &sl, const Field &f,
+                                         const Levels &lv, int k)
 {
     constexpr int U = axis_u(D), V = axis_v(D);
-    constexpr int stepU = U_EARLY ? S : 2 * S;
-    constexpr int stepV = V_EARLY ? S : 2 * S;
-    constexpr int nU = (box_ext(U) - 1) / stepU + 1;
-    constexpr int nV = (box_ext(V) - 1) / stepV + 1;
-    constexpr int nC = chunks_of(D);
-    constexpr int NSEG = nU * nV * nC;
-    constexpr int SD = box_stride(D), SU = box_stride(U), SV = box_stride(V);
-    constexpr int OD = own_stride(D), OU = own_stride(U), OV = own_stride(V);
+    constexpr int EU = ext_of(U), EV = ext_of(V);
+    constexpr int NC = chunks_of(D);
+    constexpr int BD = bstride(D), BU = bstride(U), BV = bstride(V);
+    constexpr int SD = sstride(D), SU = sstride(U), SV = sstride(V);
+    constexpr int KD = cstride(D), KU = cstride(U), KV = cstride(V);
     constexpr int l = S == 1 ? 0 : (S == 2 ? 1 : 2);
 
-    const LevelQ Lq = c.L[l];
-    const bool spline = c.spline[l] != 0;
-    const Cubic cub = c.cub[D];
-    const int R = c.R;
-    const float Rf = c.Rf;
+    // axes before D in the order sit on the s-grid, axes after it on the 2s-grid
+    const bool ue = lv.rank[U] < k, ve = lv.rank[V] < k;
+    const int stepU = ue ? S : 2 * S, stepV = ve ? S : 2 * S;
+    const int nU = ue ? count_on(EU, S) : count_on(EU, 2 * S);
+    const uint32_t mU = ue ? magic_of(count_on(EU, S)) : magic_of(count_on(EU, 2 * S));
+    int nV = ve ? count_on(EV, S) : count_on(EV, 2 * S);
+    int v0 = 0;
+    uint32_t mV = ve ? magic_of(count_on(EV, S)) : magic_of(count_on(EV, 2 * S));
+    if (V == 0 && sl.carried) {  // plane 0 is carried: skip its lines
+        v0 = 1;
+        nV -= 1;
+        mV = ve ? magic_of(count_on(EV, S) - 1) : magic_of(count_on(EV, 2 * S) - 1);
+    }
+    const int nseg = nU * nV * NC;
 
-    for (int w = threadIdx.x; w < NSEG; w += TILE_THREADS) {
-        int iu, iv, cd;
-        if (D == 2) {
-            cd = w % nC;
-            const int r = w / nC;
-            iu = r % nU;
-            iv = r / nU;
-        } else {
-            iu = w % nU;
-            const int r = w / nU;
-            cd = r % nC;
-            iv = r / nC;
-        }
+    const LevelQ Lq = lv.L[l];
+    const bool spline = lv.spline[l] != 0;
+    const Cubic cub = lv.cub[D];
+    const int R = lv.R;
+    const float Rf = lv.Rf;
+
+    for (int w = threadIdx.x; w < nseg; w += NT) {
+        // consecutive threads walk U first, then V, then the chunk along D
+        const int q1 = fdiv(w, mU);
+        const int iu = w - q1 * nU;
+        const int cd = fdiv(q1, mV);
+        const int iv = q1 - cd * nV + v0;
         const int u = iu * stepU, v = iv * stepV, dlo = 8 * cd;
-        const int gd = c.g0[D] + dlo;
-        if (c.g0[U] + u >= c.n[U] || c.g0[V] + v >= c.n[V] || gd + S > c.n[D] - 1) continue;
-        const bool owned = (u < own_ext(U)) && (v < own_ext(V));
-        float *line = box + v * SV + u * SU + dlo * SD;
-        const int lbox = v * SV + u * SU + dlo * SD;
-        const int lown = v * OV + u * OU + dlo * OD;
+        const int gd = sl.g0[D] + dlo;
+        if (sl.g0[U] + u >= f.n[U] || sl.g0[V] + v >= f.n[V] || gd + S > f.n[D] - 1) continue;
+        float *line = box + v * BV + u * BU + dlo * BD;
+        const bool owned = u < own_of(U) && v < own_of(V);
+        const int sbase = v * SV + u * SU + dlo * SD;
+        const int cbase = v * KV + u * KU + dlo * KD;
 
         auto emit = [&](int o, float p) {
             if (COMPRESS) {
-                const float x = line[o * SD];
+                const float x = line[o * BD];
                 float xr;
                 const uint32_t code = quantize(x, p, Lq, R, Rf, xr);
-                line[o * SD] = xr;
-                if (owned) {
-                    sink.own_codes[lown + o * OD] = (uint16_t)code;
-                    if (code == (uint32_t)R) {
-                        sink.central++;
-                    } else if (sink.hist_s) {
-                        atomicAdd(&sink.hist_s[code], 1u);
-                    } else if (sink.hist_g) {
-                        atomicAdd(&sink.hist_g[code], 1u);
-                    }
-                }
+                line[o * BD] = xr;
+                if (owned) sk.stage[sbase + o * SD] = (uint16_t)code;
             } else {
-                const uint32_t code = cbox[lbox + o * SD];
-                line[o * SD] = dequantize(code, p, Lq, R, line[o * SD]);
+                // outliers (code 0) already hold their stored value in the box
+                const uint32_t code = sk.cbox[cbase + o * KD];
+                const float xq = p + (float)((int)code - R) * Lq.twoe;
+                line[o * BD] = code ? xq : line[o * BD];
             }
         };
 
-        const int hi = min(8, c.n[D] - 1 - gd);  // last offset of the (possibly truncated) chunk
+        const int hi = min(8, f.n[D] - 1 - gd);  // last offset of the (possibly truncated) chunk
         if (hi == 8) {
             if (S == 4) {
-                emit(4, sp_linear(line[0], line[8 * SD]));
+                emit(4, sp_linear(line[0], line[8 * BD]));
             } else if (S == 2) {
-                const float k0 = line[0], k4 = line[4 * SD], k8 = line[8 * SD];
+                const float k0 = line[0], k4 = line[4 * BD], k8 = line[8 * BD];
                 if (spline) {
                     emit(2, sp_quad_right(k0, k4, k8));
                     emit(6, sp_quad_left(k0, k4, k8));
@@ -136,8 +233,8 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, uint16_t *__re
                     emit(6, sp_linear(k4, k8));
                 }
             } else {
-                const float k0 = line[0], k2 = line[2 * SD], k4 = line[4 * SD], k6 = line[6 * SD],
-                            k8 = line[8 * SD];
+                const float k0 = line[0], k2 = line[2 * BD], k4 = line[4 * BD], k6 = line[6 * BD],
+                            k8 = line[8 * BD];
                 if (spline) {
                     emit(1, sp_quad_right(k0, k2, k4));
                     emit(3, sp_cubic(cub, k0, k2, k4, k6));
@@ -158,20 +255,20 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, uint16_t *__re
                 const bool has_m3 = o - 3 * S >= 0;
                 const bool has_p1 = o + S <= hi;
                 const bool has_p3 = o + 3 * S <= hi;
-                const float m1 = line[(o - S) * SD];
+                const float m1 = line[(o - S) * BD];
                 float p;
                 if (!has_p1) {
                     p = m1;
                 } else {
-                    const float p1 = line[(o + S) * SD];
+                    const float p1 = line[(o + S) * BD];
                     if (!spline) {
                         p = sp_linear(m1, p1);
                     } else if (has_m3 && has_p3) {
-                        p = sp_cubic(cub, line[(o - 3 * S) * SD], m1, p1, line[(o + 3 * S) * SD]);
+                        p = sp_cubic(cub, line[(o - 3 * S) * BD], m1, p1, line[(o + 3 * S) * BD]);
                     } else if (has_m3) {
-                        p = sp_quad_left(line[(o - 3 * S) * SD], m1, p1);
+                        p = sp_quad_left(line[(o - 3 * S) * BD], m1, p1);
                     } else if (has_p3) {
-                        p = sp_quad_right(m1, p1, line[(o + 3 * S) * SD]);
+                        p = sp_quad_right(m1, p1, line[(o + 3 * S) * BD]);
                     } else {
                         p = sp_linear(m1, p1);
                     }
@@ -182,200 +279,271 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, uint16_t *__re
     }
 }
 
-template <bool COMPRESS, int O0, int O1, int O2, int S>
-__device__ __forceinline__ void run_level(float *box, uint16_t *cbox, const TileCtx &c, CompressSink &sink)
+template <bool COMPRESS, int S>
+__device__ __forceinline__ void run_level(float *box, const Sink &sk, const Slab &sl, const Field &f,
+                                          const Levels &lv)
 {
-    // pass k = 0: both other axes come later; k = 2: both earlier; k = 1: one each
-    run_pass<COMPRESS, S, O0, false, false>(box, cbox, c, sink);
-    __syncthreads();
-    run_pass<COMPRESS, S, O1, rank_in(axis_u(O1), O0, O1, O2) < 1, rank_in(axis_v(O1), O0, O1, O2) < 1>(box, cbox,
-                                                                                                      c, sink);
-    __syncthreads();
-    run_pass<COMPRESS, S, O2, true, true>(box, cbox, c, sink);
-    __syncthreads();
-}
-
-template <bool COMPRESS, int O0, int O1, int O2>
-__device__ __forceinline__ void run_levels(float *box, uint16_t *cbox, const TileCtx &c, CompressSink &sink)
-{
-    run_level<COMPRESS, O0, O1, O2, 4>(box, cbox, c, sink);
-    run_level<COMPRESS, O0, O1, O2, 2>(box, cbox, c, sink);
-    run_level<COMPRESS, O0, O1, O2, 1>(box, cbox, c, sink);
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        const int d = lv.order[k];
+        if (d == 0) run_pass<COMPRESS, S, 0>(box, sk, sl, f, lv, k);
+        else if (d == 1) run_pass<COMPRESS, S, 1>(box, sk, sl, f, lv, k);
+        else run_pass<COMPRESS, S, 2>(box, sk, sl, f, lv, k);
+        __syncthreads();
+    }
 }
 
 template <bool COMPRESS>
-__device__ void dispatch_order(int oid, float *box, uint16_t *cbox, const TileCtx &c, CompressSink &sink)
+__device__ __forceinline__ void run_slab(float *box, const Sink &sk, const Slab &sl, const Field &f,
+                                         const Levels &lv)
 {
-    switch (oid) {
-    case 0: run_levels<COMPRESS, 0, 1, 2>(box, cbox, c, sink); break;
-    case 1: run_levels<COMPRESS, 0, 2, 1>(box, cbox, c, sink); break;
-    case 2: run_levels<COMPRESS, 1, 0, 2>(box, cbox, c, sink); break;
-    case 3: run_levels<COMPRESS, 1, 2, 0>(box, cbox, c, sink); break;
-    case 4: run_levels<COMPRESS, 2, 0, 1>(box, cbox, c, sink); break;
-    default: run_levels<COMPRESS, 2, 1, 0>(box, cbox, c, sink); break;
-    }
+    run_level<COMPRESS, 4>(box, sk, sl, f, lv);
+    run_level<COMPRESS, 2>(box, sk, sl, f, lv);
+    run_level<COMPRESS, 1>(box, sk, sl, f, lv);
 }
 
-__device__ __forceinline__ int order_id(const int32_t o[3])
+// ------------------------------------------------------------ work list
+// A CTA's sequence of (item, slab): items blockIdx.x, +gridDim.x, ...; each
+// item is a run of up to f.run consecutive slabs of one column.
+struct Cursor {
+    int item, c, c_first, c_last;
+};
+
+__device__ __forceinline__ bool cursor_start(Cursor &cu, const Field &f, int item)
 {
-    // lexicographic rank of the permutation
-    if (o[0] == 0) return o[1] == 1 ? 0 : 1;
-    if (o[0] == 1) return o[1] == 0 ? 2 : 3;
-    return o[1] == 0 ? 4 : 5;
+    cu.item = item;
+    if (item >= f.items) return false;
+    const int run_id = item / f.cols;
+    cu.c_first = run_id * f.run;
+    cu.c_last = min(cu.c_first + f.run, f.slabs) - 1;
+    cu.c = cu.c_first;
+    return true;
 }
 
-__device__ __forceinline__ void tile_setup(TileCtx &c, const interp_header *hdr, Dims d, int b, int tiles_y,
-                                           int tiles_x)
+__device__ __forceinline__ bool cursor_next(Cursor &cu, const Field &f)
 {
-    const int tx = b % tiles_x;
-    const int ty = (b / tiles_x) % tiles_y;
-    const int tz = b / (tiles_x * tiles_y);
-    c.g0[0] = tz * OZ;
-    c.g0[1] = ty * OY;
-    c.g0[2] = tx * OX;
-    c.n[0] = d.nz;
-    c.n[1] = d.ny;
-    c.n[2] = d.nx;
-    for (int l = 0; l < 3; ++l) {
-        c.L[l].e = hdr->e[l];
-        c.L[l].twoe = hdr->twoe[l];
-        c.L[l].inv2e = hdr->inv2e[l];
-        c.spline[l] = hdr->cfg.level_kind[l];
-        c.cub[l] = cubic_coeffs(hdr->cfg.cubic_kind[l]);
+    if (cu.c < cu.c_last) {
+        ++cu.c;
+        return true;
     }
-    c.R = hdr->cfg.radius;
-    c.Rf = (float)c.R;
+    return cursor_start(cu, f, cu.item + gridDim.x);
+}
+
+// Bring the 9 x 17 x XP (or KP) input box of a slab into the landing buffer:
+// one TMA box (thread 0; out-of-field elements are zero-filled), or, when the
+// field's rows cannot be described by a tensor map, 4-byte cp.async copies
+// of the in-field elements by all threads.
+template <typename T, int P>
+__device__ __forceinline__ void issue_land(T *land, const T *__restrict__ src, const CUtensorMap *map, bool use_tma,
+                                           uint64_t *bar, const Field &f, const Slab &s)
+{
+    if (use_tma) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(T) * EZ * EY * P));
+            tma_load_3d(land, map, s.g0[2], s.g0[1], s.g0[0], bar);
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nzp = min(EZ, f.n[0] - s.g0[0]);
+    const int nyr = min(EY, f.n[1] - s.g0[1]);
+    const int nxc = min(EX, f.n[2] - s.g0[2]);
+    for (int r = warp; r < nzp * EY; r += NWARP) {
+        const int pz = r / EY, y = r % EY;
+        if (y >= nyr) continue;
+        const T *row = src + ((size_t)(s.g0[0] + pz) * f.n[1] + s.g0[1] + y) * f.n[2] + s.g0[2];
+        T *dst = land + r * P;
+        if (sizeof(T) == 4) {
+            if (lane < nxc) cp_async4(dst + lane, row + lane);
+            if (lane == 0 && nxc > 32) cp_async4(dst + 32, row + 32);
+        } else {
+            if (lane < nxc) dst[lane] = row[lane];
+            if (lane == 0 && nxc > 32) dst[32] = row[32];
+        }
+    }
+    cp_async_commit();
+}
+
+// Returns false if the landing transfer did not complete in time.
+__device__ __forceinline__ bool wait_land(bool use_tma, uint64_t *bar, uint32_t &phase)
+{
+    if (use_tma) {
+        const bool ok = mbar_wait_bounded(bar, phase, kTmaPolls);
+        phase ^= 1u;
+        return ok;
+    }
+    cp_async_wait_all();
+    return true;
 }
 
 // ------------------------------------------------------------ compression
-__global__ void __launch_bounds__(TILE_THREADS) k_compress(CompressArgs a, TileGrid tg)
+__global__ void __launch_bounds__(NT) k_compress(CompressArgs a, Field f, const __grid_constant__ CUtensorMap xmap,
+                                                 int use_tma)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float *box = reinterpret_cast<float *>(smem);
-    uint16_t *own_codes = reinterpret_cast<uint16_t *>(smem + kCompressCodesOff);  // 16-byte aligned rows
-    uint32_t *hist_s = reinterpret_cast<uint32_t *>(smem + kCompressHistOff);
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ Levels lv;
+    __shared__ int abort_flag;
+    float *land = reinterpret_cast<float *>(smem + C_LAND);
+    float *box = reinterpret_cast<float *>(smem + C_BOX);
+    uint16_t *stage = reinterpret_cast<uint16_t *>(smem + C_STAGE);
+    uint32_t *hist_s = reinterpret_cast<uint32_t *>(smem + C_HIST);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C_BAR);
 
-    TileCtx c;
-    tile_setup(c, a.hdr, a.dims, blockIdx.x, tg.ty, tg.tx);
-    const int nz = a.dims.nz, ny = a.dims.ny, nx = a.dims.nx;
-    const int bins = 2 * c.R;
+    const int R = a.hdr->cfg.radius;
+    const int bins = 2 * R;
     const bool smem_hist = a.hist != nullptr && bins <= HIST_SMEM_BINS;
+    if (threadIdx.x == 0) {
+        load_levels(lv, a.hdr);
+        abort_flag = 0;
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
     if (smem_hist)
-        for (int i = threadIdx.x; i < bins; i += TILE_THREADS) hist_s[i] = 0u;
-
-    // ---- stage the box (owned points + far faces) of original values
-    const bool vec = a.vec_x;
-    for (int i = threadIdx.x; i < BZ * BY * (OX / 4); i += TILE_THREADS) {
-        const int q = i % (OX / 4);
-        const int row = i / (OX / 4);
-        const int lz = row / BY, ly = row % BY;
-        const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + 4 * q;
-        if (gz >= nz || gy >= ny || gx >= nx) continue;
-        const size_t gi = ((size_t)gz * ny + gy) * nx + gx;
-        float *dst = box + (lz * BY + ly) * BX + 4 * q;
-        if (vec) {
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(a.x + gi));
-            dst[0] = v.x;
-            dst[1] = v.y;
-            dst[2] = v.z;
-            dst[3] = v.w;
-        } else {
-            for (int j = 0; j < 4 && gx + j < nx; ++j) dst[j] = __ldg(a.x + gi + j);
-        }
-    }
-    for (int row = threadIdx.x; row < BZ * BY; row += TILE_THREADS) {
-        const int lz = row / BY, ly = row % BY;
-        const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + OX;
-        if (gz >= nz || gy >= ny || gx >= nx) continue;
-        box[(lz * BY + ly) * BX + OX] = __ldg(a.x + ((size_t)gz * ny + gy) * nx + gx);
-    }
+        for (int i = threadIdx.x; i < bins; i += NT) hist_s[i] = 0u;
     __syncthreads();
 
-    CompressSink sink{own_codes, smem_hist ? hist_s : nullptr, a.hist, 0u};
+    uint32_t central = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Ay = (f.n[1] - 1) / 8 + 1, Ax = (f.n[2] - 1) / 8 + 1;
+    const int WX = (f.n[2] + 31) / 32;
+    const uint32_t RR = (uint32_t)R | ((uint32_t)R << 16);
+    const bool vec_codes = a.vec_codes;
+    uint32_t phase = 0;
 
-    // ---- anchors owned by the tile: stored losslessly, code R (Sec. IV-A)
-    {
-        const int Ay = (ny - 1) / 8 + 1, Ax = (nx - 1) / 8 + 1;
-        for (int i = threadIdx.x; i < TZ * TY * TX; i += TILE_THREADS) {
-            const int ax = i % TX, ay = (i / TX) % TY, az = i / (TX * TY);
-            const int lz = 8 * az, ly = 8 * ay, lx = 8 * ax;
-            const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + lx;
-            if (gz >= nz || gy >= ny || gx >= nx) continue;
-            a.anchors[((size_t)(gz / 8) * Ay + gy / 8) * Ax + gx / 8] = box[(lz * BY + ly) * BX + lx];
-            own_codes[(lz * OY + ly) * OX + lx] = (uint16_t)c.R;
-            sink.central++;
-        }
-    }
+    Cursor cu;
+    if (cursor_start(cu, f, blockIdx.x)) {
+        Slab sl;
+        slab_setup(sl, f, cu.item, cu.c, cu.c_first, cu.c_last);
+        issue_land<float, XP>(land, a.x, &xmap, use_tma, bar, f, sl);
+        const Sink sk{stage, nullptr};
+        for (;;) {
+            Cursor nx = cu;
+            const bool has_next = cursor_next(nx, f);
+            Slab sn = sl;
+            if (has_next) slab_setup(sn, f, nx.item, nx.c, nx.c_first, nx.c_last);
 
-    // ---- the nine passes
-    dispatch_order<true>(order_id(a.hdr->cfg.dim_order), box, nullptr, c, sink);
-
-    // ---- codes, outlier bitmap words and histogram
-    const int words_per_row = (nx + 31) / 32;
-    if (a.vec_codes) {
-        // 4 lanes per owned row, 8 codes (16 bytes) per lane
-        for (int i = threadIdx.x; i < OZ * OY * (OX / 8); i += TILE_THREADS) {
-            const int sub = i % (OX / 8);
-            const int row = i / (OX / 8);
-            const int lz = row / OY, ly = row % OY;
-            const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + 8 * sub;
-            const bool in = gz < nz && gy < ny && gx < nx;
-            uint32_t m = 0;
-            if (in) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(own_codes + row * OX + 8 * sub);
-                *reinterpret_cast<uint4 *>(a.codes + ((size_t)gz * ny + gy) * nx + gx) = v;
-                const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    m |= (uint32_t)((w4[j] & 0xffffu) == 0u) << (2 * j);
-                    m |= (uint32_t)((w4[j] >> 16) == 0u) << (2 * j + 1);
+            // ---- landed input -> compute box (planes 0..8, or 1..8 when carried)
+            if (!wait_land(use_tma, bar, phase)) abort_flag = 1;
+            if (!use_tma) __syncthreads();
+            {
+                const int pz0 = sl.carried ? 1 : 0;
+                const int nitem = (EZ - pz0) * EY * 9;  // 9 groups of 4 floats per row (x 0..35)
+                for (int i = threadIdx.x; i < nitem; i += NT) {
+                    const int row = pz0 * EY + i / 9, q = i % 9;
+                    const float4 v = *reinterpret_cast<const float4 *>(land + row * XP + 4 * q);
+                    float *d = box + row * EX + 4 * q;
+                    d[0] = v.x;
+                    if (q < 8) {
+                        d[1] = v.y;
+                        d[2] = v.z;
+                        d[3] = v.w;
+                    }
                 }
             }
-            // OX / 8 = 4 consecutive lanes form one 32-bit word
-            uint32_t word = m << (8 * sub);
-            word |= __shfl_xor_sync(0xffffffffu, word, 1);
-            word |= __shfl_xor_sync(0xffffffffu, word, 2);
-            if (sub == 0 && gz < nz && gy < ny) {
-                const int64_t wi = ((int64_t)gz * ny + gy) * words_per_row + c.g0[2] / 32;
-                a.bitmap[wi] = word;
-                if (word) atomicAdd(&a.blockcnt[wi / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
+            __syncthreads();  // box ready, landing buffer free
+            if (abort_flag) break;
+            if (has_next) issue_land<float, XP>(land, a.x, &xmap, use_tma, bar, f, sn);
+
+            run_slab<true>(box, sk, sl, f, lv);  // ends with a barrier
+
+            // ---- owned planes: codes (16-byte stores), anchors, histogram, bitmap words.
+            // A warp takes 8 consecutive rows of one plane, 4 lanes x 8 codes per row.
+            const int nzp = min(EZ, f.n[0] - sl.g0[0]);
+            const int hi = min(sl.own_hi, nzp - 1);
+            const int rows = (hi - sl.own_lo + 1) * OY;
+            const int sub = lane & 3;
+            for (int base = warp * 8; base < rows; base += NWARP * 8) {
+                const int row = base + (lane >> 2);
+                const int pz = sl.own_lo + row / OY, y = row % OY;
+                const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y;
+                const int gx = sl.g0[2] + 8 * sub;
+                const bool rin = gy < f.n[1];
+                const int nvalid = rin ? min(8, f.n[2] - gx) : 0;  // in-field codes of this lane
+                const uint32_t *srow = reinterpret_cast<const uint32_t *>(stage + pz * STAGE_PLANE + y * CP + 8 * sub);
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[j] = srow[j];
+                const size_t gi = ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
+                if (nvalid > 0 && ((pz | y) & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
+                    w[0] = (w[0] & 0xffff0000u) | (uint32_t)R;
+                    a.anchors[((size_t)(gz / 8) * Ay + gy / 8) * Ax + gx / 8] = box[pz * PLANE + y * EX + 8 * sub];
+                }
+                uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
+                if (nvalid == 8) {
+                    if (vec_codes) {
+                        *reinterpret_cast<uint4 *>(a.codes + gi) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            a.codes[gi + 2 * j] = (uint16_t)(w[j] & 0xffffu);
+                            a.codes[gi + 2 * j + 1] = (uint16_t)(w[j] >> 16);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t z = __vcmpeq2(w[j], 0u);
+                        zmask |= ((z & 1u) | ((z >> 15) & 2u)) << (2 * j);
+                        central += (uint32_t)__popc(__vcmpeq2(w[j], RR)) >> 4;
+                        const uint32_t lo = w[j] & 0xffffu, hi16 = w[j] >> 16;
+                        if (lo != (uint32_t)R && lo < (uint32_t)bins) {
+                            if (smem_hist) atomicAdd(&hist_s[lo], 1u);
+                            else if (a.hist) atomicAdd(&a.hist[lo], 1u);
+                        }
+                        if (hi16 != (uint32_t)R && hi16 < (uint32_t)bins) {
+                            if (smem_hist) atomicAdd(&hist_s[hi16], 1u);
+                            else if (a.hist) atomicAdd(&a.hist[hi16], 1u);
+                        }
+                    }
+                } else {
+                    for (int j = 0; j < nvalid; ++j) {
+                        const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                        a.codes[gi + j] = (uint16_t)c;
+                        if (c == 0u) zmask |= 1u << j;
+                        if (c == (uint32_t)R) ++central;
+                        else if (c < (uint32_t)bins) {
+                            if (smem_hist) atomicAdd(&hist_s[c], 1u);
+                            else if (a.hist) atomicAdd(&a.hist[c], 1u);
+                        }
+                    }
+                }
+                // the 4 lanes of a row assemble its 32-bit outlier word
+                uint32_t word = zmask << (8 * sub);
+                word |= __shfl_xor_sync(0xffffffffu, word, 1);
+                word |= __shfl_xor_sync(0xffffffffu, word, 2);
+                if (sub == 0 && rin) {
+                    // tile-major bitmap: a slab's words are contiguous per plane
+                    a.bitmap[((size_t)sl.col * f.n[0] + gz) * OY + y] = word;
+                    if (word) {
+                        const int64_t gw = ((int64_t)gz * f.n[1] + gy) * WX + sl.g0[2] / 32;  // global order
+                        atomicAdd(&a.blockcnt[gw / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
+                    }
+                }
             }
+            // ---- carry plane 8 into plane 0 of the next slab of the same run
+            if (has_next && nx.item == cu.item) {
+                __syncthreads();  // write-out finished reading plane 8 anchors
+                for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
+            }
+            __syncthreads();  // box and staging free for the next slab
+            if (!has_next) break;
+            cu = nx;
+            sl = sn;
         }
-    } else {
-        // one warp per owned row of 32 x-positions
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int row = warp; row < OZ * OY * (OX / 32); row += TILE_THREADS / 32) {
-            const int seg = row % (OX / 32);
-            const int r = row / (OX / 32);
-            const int lz = r / OY, ly = r % OY;
-            const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + 32 * seg + lane;
-            if (gz >= nz || gy >= ny) continue;  // warp-uniform
-            const bool in = gx < nx;
-            uint32_t code = 1;
-            if (in) {
-                code = own_codes[r * OX + 32 * seg + lane];
-                a.codes[((size_t)gz * ny + gy) * nx + gx] = (uint16_t)code;
-            }
-            const uint32_t word = __ballot_sync(0xffffffffu, in && code == 0u);
-            if (lane == 0 && c.g0[2] + 32 * seg < nx) {
-                const int64_t wi = ((int64_t)gz * ny + gy) * words_per_row + (c.g0[2] + 32 * seg) / 32;
-                a.bitmap[wi] = word;
-                if (word) atomicAdd(&a.blockcnt[wi / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
-            }
-        }
+        if (!use_tma) cp_async_wait_all();
+        if (abort_flag && threadIdx.x == 0) atomicOr(&a.hdr->status, INTERP_STATUS_TIMEOUT);
     }
 
     if (a.hist) {
-        uint32_t cnt = sink.central;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-        if ((threadIdx.x & 31) == 0 && cnt) {
-            if (smem_hist) atomicAdd(&hist_s[c.R], cnt);
-            else atomicAdd(&a.hist[c.R], cnt);
+        for (int off = 16; off > 0; off >>= 1) central += __shfl_xor_sync(0xffffffffu, central, off);
+        if (lane == 0 && central) {
+            if (smem_hist) atomicAdd(&hist_s[R], central);
+            else atomicAdd(&a.hist[R], central);
         }
         if (smem_hist) {
             __syncthreads();
-            for (int i = threadIdx.x; i < bins; i += TILE_THREADS) {
+            for (int i = threadIdx.x; i < bins; i += NT) {
                 const uint32_t h = hist_s[i];
                 if (h) atomicAdd(&a.hist[i], h);
             }
@@ -384,134 +552,243 @@ __global__ void __launch_bounds__(TILE_THREADS) k_compress(CompressArgs a, TileG
 }
 
 // ---------------------------------------------------------- decompression
-__global__ void __launch_bounds__(TILE_THREADS) k_decompress(DecompressArgs a, TileGrid tg)
+__global__ void __launch_bounds__(NT) k_decompress(DecompressArgs a, Field f, const __grid_constant__ CUtensorMap cmap,
+                                                   int use_tma)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float *box = reinterpret_cast<float *>(smem);
-    uint16_t *cbox = reinterpret_cast<uint16_t *>(smem + kDecompressCodesOff);
-
-    TileCtx c;
-    tile_setup(c, a.hdr, a.dims, blockIdx.x, tg.ty, tg.tx);
-    const int nz = a.dims.nz, ny = a.dims.ny, nx = a.dims.nx;
-
-    // ---- stage quant-codes of the whole box; outlier values for code 0
-    const bool vec = a.vec_codes;
-    for (int i = threadIdx.x; i < BZ * BY * (OX / 8); i += TILE_THREADS) {
-        const int q = i % (OX / 8);
-        const int row = i / (OX / 8);
-        const int lz = row / BY, ly = row % BY;
-        const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + 8 * q;
-        if (gz >= nz || gy >= ny || gx >= nx) continue;
-        const size_t gi = ((size_t)gz * ny + gy) * nx + gx;
-        const int li = (lz * BY + ly) * BX + 8 * q;
-        if (vec) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.codes + gi));
-            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t c0 = w4[j] & 0xffffu, c1 = w4[j] >> 16;
-                cbox[li + 2 * j] = (uint16_t)c0;
-                cbox[li + 2 * j + 1] = (uint16_t)c1;
-                if (c0 == 0u) box[li + 2 * j] = a.xrec[gi + 2 * j];
-                if (c1 == 0u) box[li + 2 * j + 1] = a.xrec[gi + 2 * j + 1];
-            }
-        } else {
-            for (int j = 0; j < 8 && gx + j < nx; ++j) {
-                const uint16_t cj = __ldg(a.codes + gi + j);
-                cbox[li + j] = cj;
-                if (cj == 0) box[li + j] = a.xrec[gi + j];
-            }
-        }
-    }
-    for (int row = threadIdx.x; row < BZ * BY; row += TILE_THREADS) {
-        const int lz = row / BY, ly = row % BY;
-        const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + OX;
-        if (gz >= nz || gy >= ny || gx >= nx) continue;
-        const size_t gi = ((size_t)gz * ny + gy) * nx + gx;
-        const uint16_t cj = __ldg(a.codes + gi);
-        cbox[(lz * BY + ly) * BX + OX] = cj;
-        if (cj == 0) box[(lz * BY + ly) * BX + OX] = a.xrec[gi];
-    }
-    // anchors of the box, including the borrowed ones on the far faces
-    {
-        const int Ay = (ny - 1) / 8 + 1, Ax = (nx - 1) / 8 + 1;
-        for (int i = threadIdx.x; i < (TZ + 1) * (TY + 1) * (TX + 1); i += TILE_THREADS) {
-            const int ax = i % (TX + 1), ay = (i / (TX + 1)) % (TY + 1), az = i / ((TX + 1) * (TY + 1));
-            const int lz = 8 * az, ly = 8 * ay, lx = 8 * ax;
-            const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + lx;
-            if (gz >= nz || gy >= ny || gx >= nx) continue;
-            box[(lz * BY + ly) * BX + lx] = __ldg(a.anchors + ((size_t)(gz / 8) * Ay + gy / 8) * Ax + gx / 8);
-        }
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ Levels lv;
+    __shared__ int abort_flag;
+    uint16_t *land = reinterpret_cast<uint16_t *>(smem + D_LAND);
+    float *box = reinterpret_cast<float *>(smem + D_BOX);
+    uint16_t *cbox = reinterpret_cast<uint16_t *>(smem + D_CBOX);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + D_BAR);
+    if (threadIdx.x == 0) {
+        load_levels(lv, a.hdr);
+        abort_flag = 0;
+        mbar_init(bar, 1);
+        fence_barrier_init();
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int Ay = (f.n[1] - 1) / 8 + 1, Ax = (f.n[2] - 1) / 8 + 1;
+    const bool vec_x = a.vec_xrec;
+    uint32_t phase = 0;
 
-    CompressSink sink{nullptr, nullptr, nullptr, 0u};
-    dispatch_order<false>(order_id(a.hdr->cfg.dim_order), box, cbox, c, sink);
+    Cursor cu;
+    if (!cursor_start(cu, f, blockIdx.x)) return;
+    Slab sl;
+    slab_setup(sl, f, cu.item, cu.c, cu.c_first, cu.c_last);
+    issue_land<uint16_t, KP>(land, a.codes, &cmap, use_tma, bar, f, sl);
+    const Sink sk{nullptr, cbox};
+    for (;;) {
+        Cursor nx = cu;
+        const bool has_next = cursor_next(nx, f);
+        Slab sn = sl;
+        if (has_next) slab_setup(sn, f, nx.item, nx.c, nx.c_first, nx.c_last);
 
-    // ---- write the owned reconstruction
-    const bool vec4 = a.vec_xrec;
-    for (int i = threadIdx.x; i < OZ * OY * (OX / 4); i += TILE_THREADS) {
-        const int q = i % (OX / 4);
-        const int row = i / (OX / 4);
-        const int lz = row / OY, ly = row % OY;
-        const int gz = c.g0[0] + lz, gy = c.g0[1] + ly, gx = c.g0[2] + 4 * q;
-        if (gz >= nz || gy >= ny || gx >= nx) continue;
-        const size_t gi = ((size_t)gz * ny + gy) * nx + gx;
-        const float *src = box + (lz * BY + ly) * BX + 4 * q;
-        if (vec4) {
-            *reinterpret_cast<float4 *>(a.xrec + gi) = make_float4(src[0], src[1], src[2], src[3]);
-        } else {
-            for (int j = 0; j < 4 && gx + j < nx; ++j) a.xrec[gi + j] = src[j];
+        // ---- landed codes -> code box; outliers' stored values and anchors -> value box
+        if (!wait_land(use_tma, bar, phase)) abort_flag = 1;
+        if (!use_tma) __syncthreads();
+        {
+            const int pz0 = sl.carried ? 1 : 0;
+            const int nzp = min(EZ, f.n[0] - sl.g0[0]);
+            const int nyr = min(EY, f.n[1] - sl.g0[1]);
+            const int nxc = min(EX, f.n[2] - sl.g0[2]);
+            const int nitem = (EZ - pz0) * EY * 5;  // 5 groups of 8 codes per row (x 0..39)
+            for (int i = threadIdx.x; i < nitem; i += NT) {
+                const int row = pz0 * EY + i / 5, q = i % 5;
+                const uint4 v = *reinterpret_cast<const uint4 *>(land + row * KP + 8 * q);
+                uint32_t *d = reinterpret_cast<uint32_t *>(cbox + row * CP + 8 * q);
+                d[0] = v.x;
+                if (q < 4) {
+                    d[1] = v.y;
+                    d[2] = v.z;
+                    d[3] = v.w;
+                }
+                // code 0 marks an outlier: its stored value was scattered into xrec
+                const uint32_t z = __vcmpeq2(v.x, 0u) | __vcmpeq2(v.y, 0u) | __vcmpeq2(v.z, 0u) | __vcmpeq2(v.w, 0u);
+                const int pz = row / EY, y = row % EY;
+                if (z && pz < nzp && y < nyr) {
+                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                    for (int j = 0; j < 8 && 8 * q + j < min(nxc, EX); ++j) {
+                        if (((wv[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) {
+                            const size_t g = ((size_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * f.n[2] + sl.g0[2] +
+                                             8 * q + j;
+                            box[row * EX + 8 * q + j] = __ldg(a.xrec + g);
+                        }
+                    }
+                }
+            }
+            // anchors of planes 8 and, when not carried, 0
+            for (int i = threadIdx.x; i < 2 * 3 * 5; i += NT) {
+                const int az = i / 15, ay = (i / 5) % 3, ax = i % 5;
+                const int pz = 8 * az, y = 8 * ay, x = 8 * ax;
+                if ((az == 0 && sl.carried) || pz >= nzp || y >= nyr || x >= nxc) continue;
+                const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gxx = sl.g0[2] + x;
+                box[pz * PLANE + y * EX + x] = __ldg(a.anchors + ((size_t)(gz / 8) * Ay + gy / 8) * Ax + gxx / 8);
+            }
         }
+        __syncthreads();  // code box and anchors ready, landing buffer free
+        if (abort_flag) break;
+        if (has_next) issue_land<uint16_t, KP>(land, a.codes, &cmap, use_tma, bar, f, sn);
+
+        run_slab<false>(box, sk, sl, f, lv);  // ends with a barrier
+
+        // ---- write the owned planes: 8 lanes x 4 values per row, 4 rows per warp
+        const int nzp = min(EZ, f.n[0] - sl.g0[0]);
+        const int hi = min(sl.own_hi, nzp - 1);
+        const int rows = (hi - sl.own_lo + 1) * OY;
+        const int sub = lane & 7;
+        for (int base = warp * 4; base < rows; base += NWARP * 4) {
+            const int row = base + (lane >> 3);
+            const int pz = sl.own_lo + row / OY, y = row % OY;
+            const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gx = sl.g0[2] + 4 * sub;
+            if (gy >= f.n[1] || gx >= f.n[2]) continue;
+            const float *s4 = box + pz * PLANE + y * EX + 4 * sub;
+            float *dst = a.xrec + ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
+            if (vec_x && gx + 3 < f.n[2]) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(s4[0], s4[1], s4[2], s4[3]);
+            } else {
+                for (int j = 0; j < 4 && gx + j < f.n[2]; ++j) dst[j] = s4[j];
+            }
+        }
+        __syncthreads();  // every thread is done reading the box
+        if (!has_next) break;
+        // ---- carry plane 8 into plane 0 of the next slab of the same run
+        if (nx.item == cu.item) {
+            for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
+            __syncthreads();
+        }
+        cu = nx;
+        sl = sn;
     }
+    if (!use_tma) cp_async_wait_all();
+    if (abort_flag && threadIdx.x == 0) atomicOr(&const_cast<interp_header *>(a.hdr)->status, INTERP_STATUS_TIMEOUT);
 }
 
-
-// The dynamic shared-memory opt-in is a per-device function attribute: set it
-// once for every device the library is used on.
+// ------------------------------------------------------------ host side
 constexpr int kMaxDevices = 64;
-volatile int compress_attr_done[kMaxDevices];
-volatile int decompress_attr_done[kMaxDevices];
+int compress_grid[kMaxDevices];
+int decompress_grid[kMaxDevices];
 
+// Opt in to the kernel's dynamic shared memory and size the persistent grid
+// (resident CTAs per SM x SMs), once per device.
 template <typename K>
-cudaError_t ensure_smem_attr(K kernel, size_t bytes, volatile int *done)
+cudaError_t prepare(K kernel, size_t smem, int *cache, int &grid)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < kMaxDevices && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev] = 1;
-    return e;
+    if (dev >= 0 && dev < kMaxDevices && cache[dev] > 0) {
+        grid = cache[dev];
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    grid = per_sm * sm_count();
+    if (dev >= 0 && dev < kMaxDevices) cache[dev] = grid;
+    return cudaSuccess;
 }
 
-TileGrid tile_grid(Dims d)
+// Split the slabs of every column into runs so that the busiest CTA of the
+// persistent grid has the least work (each run start recomputes one plane).
+Field plan(Dims d, int grid)
 {
-    return TileGrid{(d.nz + OZ - 1) / OZ, (d.ny + OY - 1) / OY, (d.nx + OX - 1) / OX};
+    Field f;
+    f.n[0] = d.nz;
+    f.n[1] = d.ny;
+    f.n[2] = d.nx;
+    f.cols_x = (d.nx + OX - 1) / OX;
+    f.cols = f.cols_x * ((d.ny + OY - 1) / OY);
+    f.slabs = d.nz > 1 ? (d.nz - 1 + 7) / 8 : 1;
+    int best_run = f.slabs;
+    double best = 1e300;
+    for (int run = 1; run <= f.slabs; ++run) {
+        const long long items = (long long)f.cols * ((f.slabs + run - 1) / run);
+        const long long per_cta = (items + grid - 1) / grid;
+        const double cost = (double)per_cta * (run + 0.15);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_run = run;
+        }
+    }
+    f.run = best_run;
+    f.items = f.cols * ((f.slabs + f.run - 1) / f.run);
+    return f;
 }
 
 }  // namespace
 
+size_t bitmap_words_tiled(Dims d)
+{
+    const size_t cols = (size_t)((d.nx + OX - 1) / OX) * (size_t)((d.ny + OY - 1) / OY);
+    return cols * (size_t)d.nz * OY;
+}
+
 cudaError_t launch_compress_tiles(const CompressArgs &a, cudaStream_t s)
 {
-    cudaError_t e = ensure_smem_attr(k_compress, kCompressSmem, compress_attr_done);
+    int grid = 0;
+    cudaError_t e = prepare(k_compress, kCompressSmem, compress_grid, grid);
     if (e != cudaSuccess) return e;
-    const TileGrid tg = tile_grid(a.dims);
-    const long long n = (long long)tg.tz * tg.ty * tg.tx;
-    if (n <= 0) return cudaSuccess;
-    k_compress<<<(unsigned)n, TILE_THREADS, kCompressSmem, s>>>(a, tg);
+    const Field f = plan(a.dims, grid);
+    if (f.items < grid) grid = f.items;
+    CUtensorMap map;
+    const uint32_t box[3] = {XP, EY, EZ};
+    const int use_tma = encode_tensor_map_3d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.x, a.dims, box) ? 1 : 0;
+    if (!use_tma) std::memset(&map, 0, sizeof(map));
+    k_compress<<<grid, NT, kCompressSmem, s>>>(a, f, map, use_tma);
     return cudaGetLastError();
 }
 
 cudaError_t launch_decompress_tiles(const DecompressArgs &a, cudaStream_t s)
 {
-    cudaError_t e = ensure_smem_attr(k_decompress, kDecompressSmem, decompress_attr_done);
+    int grid = 0;
+    cudaError_t e = prepare(k_decompress, kDecompressSmem, decompress_grid, grid);
     if (e != cudaSuccess) return e;
-    const TileGrid tg = tile_grid(a.dims);
-    const long long n = (long long)tg.tz * tg.ty * tg.tx;
-    if (n <= 0) return cudaSuccess;
-    k_decompress<<<(unsigned)n, TILE_THREADS, kDecompressSmem, s>>>(a, tg);
+    const Field f = plan(a.dims, grid);
+    if (f.items < grid) grid = f.items;
+    CUtensorMap map;
+    const uint32_t box[3] = {KP, EY, EZ};
+    const int use_tma =
+        encode_tensor_map_3d(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.codes, a.dims, box) ? 1 : 0;
+    if (!use_tma) std::memset(&map, 0, sizeof(map));
+    k_decompress<<<grid, NT, kDecompressSmem, s>>>(a, f, map, use_tma);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ tensor maps
+bool encode_tensor_map_3d(CUtensorMap *map, CUtensorMapDataType dtype, size_t elem, const void *base, Dims d,
+                          const uint32_t box[3])
+{
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+        looked_up = true;
+    }
+    if (!fn) return false;
+    const size_t row_bytes = elem * (size_t)d.nx;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || row_bytes % 16 != 0) return false;
+    const cuuint64_t gdim[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+    const cuuint64_t gstride[2] = {(cuuint64_t)row_bytes, (cuuint64_t)row_bytes * (cuuint64_t)d.ny};
+    const cuuint32_t bdim[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult r = fn(map, dtype, 3, const_cast<void *>(base), gdim, gstride, bdim, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 }  // namespace gi

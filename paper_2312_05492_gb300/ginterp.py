@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libginterp.so")
 
 INTERP_OK, INTERP_EINVAL, INTERP_ECUDA, INTERP_EWORKSPACE, INTERP_ECAPACITY, INTERP_ENONFINITE = 0, -1, -2, -3, -4, -5
-STATUS_CAPACITY, STATUS_NONFINITE = 1, 2
+STATUS_CAPACITY, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 
 FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress", "interp_decompress",
              "qcode_histogram", "interp_autotune", "interp_timing_enable", "interp_timing_read",

@@ -157,7 +157,9 @@ struct Sink {
     const uint16_t *cbox;  // decompression: code box
 };
 
-template <bool COMPRESS, int S, int D>
+// INTERIOR: the slab's whole box lies inside the field and every chunk is
+// full, so no line or chunk needs the field-edge checks.
+template <bool COMPRESS, bool INTERIOR, int S, int D>
 __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk, const Slab &sl, const Field &f,
                                          const Levels &lv, int k)
 {
@@ -183,6 +185,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
         mV = ve ? magic_of(count_on(EV, S) - 1) : magic_of(count_on(EV, 2 * S) - 1);
     }
     const int nseg = nU * nV * NC;
+    if ((int)threadIdx.x >= nseg) return;  // no segment for this thread in this pass
 
     const LevelQ Lq = lv.L[l];
     const bool spline = lv.spline[l] != 0;
@@ -198,7 +201,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
         const int iv = q1 - cd * nV + v0;
         const int u = iu * stepU, v = iv * stepV, dlo = 8 * cd;
         const int gd = sl.g0[D] + dlo;
-        if (sl.g0[U] + u >= f.n[U] || sl.g0[V] + v >= f.n[V] || gd + S > f.n[D] - 1) continue;
+        if (!INTERIOR && (sl.g0[U] + u >= f.n[U] || sl.g0[V] + v >= f.n[V] || gd + S > f.n[D] - 1)) continue;
         float *line = box + v * BV + u * BU + dlo * BD;
         const bool owned = u < own_of(U) && v < own_of(V);
         const int sbase = v * SV + u * SU + dlo * SD;
@@ -219,7 +222,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
             }
         };
 
-        const int hi = min(8, f.n[D] - 1 - gd);  // last offset of the (possibly truncated) chunk
+        const int hi = INTERIOR ? 8 : min(8, f.n[D] - 1 - gd);  // last offset of the (possibly truncated) chunk
         if (hi == 8) {
             if (S == 4) {
                 emit(4, sp_linear(line[0], line[8 * BD]));
@@ -279,16 +282,16 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
     }
 }
 
-template <bool COMPRESS, int S>
+template <bool COMPRESS, bool INTERIOR, int S>
 __device__ __forceinline__ void run_level(float *box, const Sink &sk, const Slab &sl, const Field &f,
                                           const Levels &lv)
 {
 #pragma unroll 1
     for (int k = 0; k < 3; ++k) {
         const int d = lv.order[k];
-        if (d == 0) run_pass<COMPRESS, S, 0>(box, sk, sl, f, lv, k);
-        else if (d == 1) run_pass<COMPRESS, S, 1>(box, sk, sl, f, lv, k);
-        else run_pass<COMPRESS, S, 2>(box, sk, sl, f, lv, k);
+        if (d == 0) run_pass<COMPRESS, INTERIOR, S, 0>(box, sk, sl, f, lv, k);
+        else if (d == 1) run_pass<COMPRESS, INTERIOR, S, 1>(box, sk, sl, f, lv, k);
+        else run_pass<COMPRESS, INTERIOR, S, 2>(box, sk, sl, f, lv, k);
         __syncthreads();
     }
 }
@@ -297,9 +300,16 @@ template <bool COMPRESS>
 __device__ __forceinline__ void run_slab(float *box, const Sink &sk, const Slab &sl, const Field &f,
                                          const Levels &lv)
 {
-    run_level<COMPRESS, 4>(box, sk, sl, f, lv);
-    run_level<COMPRESS, 2>(box, sk, sl, f, lv);
-    run_level<COMPRESS, 1>(box, sk, sl, f, lv);
+    const bool interior = sl.g0[0] + 8 <= f.n[0] - 1 && sl.g0[1] + OY <= f.n[1] - 1 && sl.g0[2] + OX <= f.n[2] - 1;
+    if (interior) {
+        run_level<COMPRESS, true, 4>(box, sk, sl, f, lv);
+        run_level<COMPRESS, true, 2>(box, sk, sl, f, lv);
+        run_level<COMPRESS, true, 1>(box, sk, sl, f, lv);
+    } else {
+        run_level<COMPRESS, false, 4>(box, sk, sl, f, lv);
+        run_level<COMPRESS, false, 2>(box, sk, sl, f, lv);
+        run_level<COMPRESS, false, 1>(box, sk, sl, f, lv);
+    }
 }
 
 // ------------------------------------------------------------ work list

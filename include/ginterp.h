@@ -45,7 +45,9 @@ typedef enum {
     INTERP_ECUDA = -2,      /* a CUDA launch or runtime call failed */
     INTERP_EWORKSPACE = -3, /* workspace smaller than interp_workspace_bytes() */
     INTERP_ECAPACITY = -4,  /* (host helper) outlier count exceeds out_capacity */
-    INTERP_ENONFINITE = -5  /* (host helper) non-finite input values were found */
+    INTERP_ENONFINITE = -5, /* (host helper) non-finite input values were found */
+    INTERP_ESCRATCH = -6    /* interp_compress_noalloc: the field needs more scratch than the
+                               library's built-in array (interp_noalloc_scratch_bytes()) */
 } interp_status;
 
 /* device-side status bits (interp_header.status) */
@@ -151,6 +153,26 @@ int interp_autotune(const float *d_x, const int64_t dims[3], interp_config *h_cf
 int interp_timing_enable(int on);
 int interp_timing_read(double *compress_ms, int32_t *compress_launches, double *decompress_ms,
                        int32_t *decompress_launches);
+
+/* Compression without any caller-provided scratch (no counterpart in the paper).
+ * For callers that cannot allocate device memory: their device memory belongs to an
+ * allocator they cannot ask for more, they run in a host that forbids device allocation,
+ * or they must never pay for a cudaMalloc and its synchronisation.  Same arguments and
+ * results as interp_compress without d_ws / ws_bytes: the scratch is an array compiled
+ * into the library (interp_noalloc_scratch_bytes() bytes, 24 MiB, held on every GPU that
+ * loads the library until the process exits).  Fields whose interp_workspace_bytes()
+ * exceed it are rejected with INTERP_ESCRATCH before any work is enqueued.  The first
+ * call on a device (with that device current) looks up the array's device address; make
+ * that first call before any stream capture.  Every call reuses the same array and clears
+ * what must start at zero itself; calls whose work overlaps on the GPU race on it.  Not
+ * thread-safe.  Allocates and frees nothing. */
+int interp_compress_noalloc(const float *d_x, const int64_t dims[3], double eb, const interp_config *cfg,
+                            float *d_anchors, uint16_t *d_codes, uint32_t *d_out_idx, float *d_out_val,
+                            uint64_t out_capacity, uint32_t *d_hist, interp_header *d_hdr,
+                            interp_stream_t stream);
+
+/* Size in bytes of the built-in scratch array used by interp_compress_noalloc. */
+size_t interp_noalloc_scratch_bytes(void);
 
 /* Human-readable text for an interp_status value. */
 const char *interp_status_string(int status);

@@ -265,6 +265,7 @@ const char *interp_status_string(int status)
     case INTERP_EWORKSPACE: return "workspace too small";
     case INTERP_ECAPACITY: return "outlier capacity exceeded";
     case INTERP_ENONFINITE: return "non-finite input";
+    case INTERP_ESCRATCH: return "field too large for the built-in no-allocation scratch";
     default: return "unknown status";
     }
 }

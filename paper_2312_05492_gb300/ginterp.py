@@ -19,11 +19,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libginterp.so")
 
 INTERP_OK, INTERP_EINVAL, INTERP_ECUDA, INTERP_EWORKSPACE, INTERP_ECAPACITY, INTERP_ENONFINITE = 0, -1, -2, -3, -4, -5
+INTERP_ESCRATCH = -6
 STATUS_CAPACITY, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 
 FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress", "interp_decompress",
              "qcode_histogram", "interp_autotune", "interp_timing_enable", "interp_timing_read",
-             "interp_status_string")
+             "interp_compress_noalloc", "interp_noalloc_scratch_bytes", "interp_status_string")
 
 # kernels each call launches (memsets excluded): compress = [profile] + range or
 # header + tiles + outlier scan + outlier write; decompress = scatter + tiles
@@ -83,6 +84,10 @@ def load() -> ctypes.CDLL:
     lib.interp_timing_enable.argtypes = [ctypes.c_int]
     lib.interp_timing_read.restype = ctypes.c_int
     lib.interp_timing_read.argtypes = [P, P, P, P]
+    lib.interp_compress_noalloc.restype = ctypes.c_int
+    lib.interp_compress_noalloc.argtypes = [P, dims_t, ctypes.c_double, cfg_p, P, P, P, P, u64, P, P, P]
+    lib.interp_noalloc_scratch_bytes.restype = ctypes.c_size_t
+    lib.interp_noalloc_scratch_bytes.argtypes = []
     lib.interp_status_string.restype = ctypes.c_char_p
     lib.interp_status_string.argtypes = [ctypes.c_int]
     _lib = lib
@@ -144,6 +149,18 @@ def interp_timing_read():
     _check(load().interp_timing_read(ctypes.byref(cm), ctypes.byref(cn), ctypes.byref(dm), ctypes.byref(dn)),
            "interp_timing_read")
     return cm.value, cn.value, dm.value, dn.value
+
+
+def interp_compress_noalloc(d_x, dims, eb, cfg, d_anchors, d_codes, d_out_idx, d_out_val, out_capacity, d_hist,
+                            d_hdr, stream) -> int:
+    """interp_compress for callers that cannot allocate device memory: the scratch is the
+    library's built-in array (interp_noalloc_scratch_bytes()), shared by all calls."""
+    return load().interp_compress_noalloc(d_x, _dims(dims), float(eb), ctypes.byref(cfg), d_anchors, d_codes,
+                                          d_out_idx, d_out_val, int(out_capacity), d_hist, d_hdr, stream)
+
+
+def interp_noalloc_scratch_bytes() -> int:
+    return int(load().interp_noalloc_scratch_bytes())
 
 
 def interp_status_string(rc: int) -> str:

@@ -130,6 +130,43 @@ int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const f
                       const uint16_t *d_codes, const uint32_t *d_out_idx, const float *d_out_val,
                       uint64_t out_capacity, float *d_xrec, interp_stream_t stream);
 
+/* Batched forms: n fields of any (uneven) shapes, bounds and configurations in one call.
+ * Each item carries exactly the arguments of the single-field call (its own workspace).
+ * Per-field setup (range, profile, bounds) and outlier compaction are enqueued per field;
+ * the tile work of all fields runs in ONE persistent kernel launch whose CTAs take work
+ * items (runs of 8-plane slabs of 16 x 32 columns) from all fields.  Results are identical,
+ * bit for bit, to n single calls.  1 <= n <= 16.  Stream-ordered, no synchronisation;
+ * capturable into a CUDA graph after one warm-up call on the device. */
+typedef struct {
+    const float *d_x;
+    int64_t dims[3];
+    double eb;
+    interp_config cfg;
+    float *d_anchors;
+    uint16_t *d_codes;
+    uint32_t *d_out_idx;
+    float *d_out_val;
+    uint64_t out_capacity;
+    uint32_t *d_hist;
+    interp_header *d_hdr;
+    void *d_ws;
+    size_t ws_bytes;
+} interp_compress_item;
+
+typedef struct {
+    int64_t dims[3];
+    const interp_header *d_hdr;
+    const float *d_anchors;
+    const uint16_t *d_codes;
+    const uint32_t *d_out_idx;
+    const float *d_out_val;
+    uint64_t out_capacity;
+    float *d_xrec;
+} interp_decompress_item;
+
+int interp_compress_batched(const interp_compress_item *h_items, int n, interp_stream_t stream);
+int interp_decompress_batched(const interp_decompress_item *h_items, int n, interp_stream_t stream);
+
 /* Histogram of quant-codes (Fig. 1 "histogram", Sec. V-A): d_hist[c] = #{i : codes[i] = c}
  * for c in [0, 2R); d_hist (2R uint32) is zeroed by the callee.  Codes >= 2R are ignored. */
 int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_t *d_hist,

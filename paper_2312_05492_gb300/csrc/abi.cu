@@ -129,47 +129,107 @@ size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg)
     return ws_layout(dims).total;
 }
 
+int interp_compress_batched(const interp_compress_item *items, int n, interp_stream_t stream)
+{
+    if (!items || n < 1 || n > gi::kMaxBatch) return INTERP_EINVAL;
+    WsLayout L[gi::kMaxBatch];
+    for (int i = 0; i < n; ++i) {  // every argument is checked before anything is enqueued
+        const interp_compress_item &it = items[i];
+        if (!dims_ok(it.dims) || !cfg_ok(&it.cfg)) return INTERP_EINVAL;
+        if (!(it.eb > 0.0) || std::isinf(it.eb)) return INTERP_EINVAL;
+        if (!it.d_x || !it.d_anchors || !it.d_codes || !it.d_hdr || !it.d_ws) return INTERP_EINVAL;
+        if (it.out_capacity > 0 && (!it.d_out_idx || !it.d_out_val)) return INTERP_EINVAL;
+        L[i] = ws_layout(it.dims);
+        if (it.ws_bytes < L[i].total) return INTERP_EWORKSPACE;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    gi::CompressArgs args[gi::kMaxBatch];
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const interp_compress_item &it = items[i];
+        const interp_config &c = it.cfg;
+        const Dims d = to_dims(it.dims);
+        const double alpha = effective_alpha(c, it.eb);
+        unsigned char *ws = static_cast<unsigned char *>(it.d_ws);
+        unsigned int *counter = reinterpret_cast<unsigned int *>(ws + L[i].ctrl);
+        uint32_t *bitmap = reinterpret_cast<uint32_t *>(ws + L[i].bitmap);
+        uint32_t *blockcnt = reinterpret_cast<uint32_t *>(ws + L[i].blockcnt);
+        e = cudaMemsetAsync(ws + L[i].ctrl, 0, kCtrlBytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(blockcnt, 0, sizeof(uint32_t) * (size_t)L[i].nblk, s);
+        if (e == cudaSuccess && it.d_hist)
+            e = cudaMemsetAsync(it.d_hist, 0, sizeof(uint32_t) * 2 * (size_t)c.radius, s);
+        if (e == cudaSuccess && c.autotune) e = gi::launch_profile(it.d_x, d, it.d_hdr, 1, s);
+        if (e == cudaSuccess) {
+            if (c.eb_mode)
+                e = gi::launch_range(it.d_x, d, it.eb, c, alpha, it.d_hdr, ws + L[i].partials, counter,
+                                     gi::range_blocks(), s);
+            else
+                e = gi::launch_header_init(it.d_hdr, d, it.eb, c, alpha, s);
+        }
+        args[i] = gi::CompressArgs{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
+                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0};
+    }
+    if (e == cudaSuccess) {
+        timing_mark(0, 0, s);
+        e = gi::launch_compress_tiles(args, n, s);  // one persistent launch for every field
+        timing_mark(0, 1, s);
+    }
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const interp_compress_item &it = items[i];
+        e = gi::launch_outlier_compaction(args[i].bitmap, args[i].blockcnt, L[i].words, args[i].dims, it.d_x,
+                                          it.d_out_idx, it.d_out_val, it.out_capacity, it.d_hdr, s);
+    }
+    return cuda_status(e);
+}
+
 int interp_compress(const float *d_x, const int64_t dims[3], double eb, const interp_config *cfg,
                     float *d_anchors, uint16_t *d_codes, uint32_t *d_out_idx, float *d_out_val,
                     uint64_t out_capacity, uint32_t *d_hist, interp_header *d_hdr, void *d_ws, size_t ws_bytes,
                     interp_stream_t stream)
 {
-    if (!dims_ok(dims) || !cfg_ok(cfg)) return INTERP_EINVAL;
-    if (!(eb > 0.0) || std::isinf(eb)) return INTERP_EINVAL;
-    if (!d_x || !d_anchors || !d_codes || !d_hdr || !d_ws) return INTERP_EINVAL;
-    if (out_capacity > 0 && (!d_out_idx || !d_out_val)) return INTERP_EINVAL;
-    const WsLayout L = ws_layout(dims);
-    if (ws_bytes < L.total) return INTERP_EWORKSPACE;
+    if (!dims_ok(dims) || !cfg) return INTERP_EINVAL;
+    interp_compress_item it;
+    it.d_x = d_x;
+    for (int a = 0; a < 3; ++a) it.dims[a] = dims[a];
+    it.eb = eb;
+    it.cfg = *cfg;
+    it.d_anchors = d_anchors;
+    it.d_codes = d_codes;
+    it.d_out_idx = d_out_idx;
+    it.d_out_val = d_out_val;
+    it.out_capacity = out_capacity;
+    it.d_hist = d_hist;
+    it.d_hdr = d_hdr;
+    it.d_ws = d_ws;
+    it.ws_bytes = ws_bytes;
+    return interp_compress_batched(&it, 1, stream);
+}
 
+int interp_decompress_batched(const interp_decompress_item *items, int n, interp_stream_t stream)
+{
+    if (!items || n < 1 || n > gi::kMaxBatch) return INTERP_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const interp_decompress_item &it = items[i];
+        if (!dims_ok(it.dims)) return INTERP_EINVAL;
+        if (!it.d_hdr || !it.d_anchors || !it.d_codes || !it.d_xrec) return INTERP_EINVAL;
+        if (it.out_capacity > 0 && (!it.d_out_idx || !it.d_out_val)) return INTERP_EINVAL;
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const interp_config c = *cfg;
-    const Dims d = to_dims(dims);
-    const double alpha = effective_alpha(c, eb);
-    unsigned char *ws = static_cast<unsigned char *>(d_ws);
-    unsigned int *counter = reinterpret_cast<unsigned int *>(ws + L.ctrl);
-    uint32_t *bitmap = reinterpret_cast<uint32_t *>(ws + L.bitmap);
-    uint32_t *blockcnt = reinterpret_cast<uint32_t *>(ws + L.blockcnt);
-
-    cudaError_t e = cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(blockcnt, 0, sizeof(uint32_t) * (size_t)L.nblk, s);
-    if (e == cudaSuccess && d_hist) e = cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * 2 * (size_t)c.radius, s);
-    if (e == cudaSuccess && c.autotune) e = gi::launch_profile(d_x, d, d_hdr, 1, s);
-    if (e == cudaSuccess) {
-        if (c.eb_mode)
-            e = gi::launch_range(d_x, d, eb, c, alpha, d_hdr, ws + L.partials, counter, gi::range_blocks(), s);
-        else
-            e = gi::launch_header_init(d_hdr, d, eb, c, alpha, s);
+    gi::DecompressArgs args[gi::kMaxBatch];
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const interp_decompress_item &it = items[i];
+        const Dims d = to_dims(it.dims);
+        if (it.out_capacity > 0)
+            e = gi::launch_outlier_scatter(it.d_hdr, it.d_out_idx, it.d_out_val, it.out_capacity, it.d_xrec, s);
+        args[i] = gi::DecompressArgs{d, it.d_anchors, it.d_codes, it.d_xrec, it.d_hdr,
+                                     gi::aligned16(it.d_xrec) && d.nx % 4 == 0};
     }
     if (e == cudaSuccess) {
-        gi::CompressArgs a{d_x, d, d_anchors, d_codes, bitmap, blockcnt, d_hist, c.radius, d_hdr,
-                           gi::aligned16(d_codes) && d.nx % 8 == 0};
-        timing_mark(0, 0, s);
-        e = gi::launch_compress_tiles(a, s);
-        timing_mark(0, 1, s);
+        timing_mark(1, 0, s);
+        e = gi::launch_decompress_tiles(args, n, s);  // one persistent launch for every field
+        timing_mark(1, 1, s);
     }
-    if (e == cudaSuccess)
-        e = gi::launch_outlier_compaction(bitmap, blockcnt, L.words, d, d_x, d_out_idx, d_out_val, out_capacity,
-                                          d_hdr, s);
     return cuda_status(e);
 }
 
@@ -178,19 +238,16 @@ int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const f
                       uint64_t out_capacity, float *d_xrec, interp_stream_t stream)
 {
     if (!dims_ok(dims)) return INTERP_EINVAL;
-    if (!d_hdr || !d_anchors || !d_codes || !d_xrec) return INTERP_EINVAL;
-    if (out_capacity > 0 && (!d_out_idx || !d_out_val)) return INTERP_EINVAL;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const Dims d = to_dims(dims);
-    cudaError_t e = cudaSuccess;
-    if (out_capacity > 0) e = gi::launch_outlier_scatter(d_hdr, d_out_idx, d_out_val, out_capacity, d_xrec, s);
-    if (e == cudaSuccess) {
-        gi::DecompressArgs a{d, d_anchors, d_codes, d_xrec, d_hdr, gi::aligned16(d_xrec) && d.nx % 4 == 0};
-        timing_mark(1, 0, s);
-        e = gi::launch_decompress_tiles(a, s);
-        timing_mark(1, 1, s);
-    }
-    return cuda_status(e);
+    interp_decompress_item it;
+    for (int a = 0; a < 3; ++a) it.dims[a] = dims[a];
+    it.d_hdr = d_hdr;
+    it.d_anchors = d_anchors;
+    it.d_codes = d_codes;
+    it.d_out_idx = d_out_idx;
+    it.d_out_val = d_out_val;
+    it.out_capacity = out_capacity;
+    it.d_xrec = d_xrec;
+    return interp_decompress_batched(&it, 1, stream);
 }
 
 int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_t *d_hist, interp_stream_t stream)

@@ -34,6 +34,9 @@ constexpr int BITMAP_BLOCK_WORDS = 2048;  // words per compaction block
 // histogram bins kept in shared memory by the fused histogram
 constexpr int HIST_SMEM_BINS = 1024;
 
+// fields per batched call (one persistent tile launch covers all of them)
+constexpr int kMaxBatch = 16;
+
 // ------------------------------------------------------------- parameters
 struct Dims {
     int nz, ny, nx;
@@ -130,8 +133,9 @@ cudaError_t launch_header_init(interp_header *hdr, Dims d, double eb, interp_con
 cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s);
 cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, double alpha, interp_header *hdr,
                          void *partials, unsigned int *counter, int nblocks, cudaStream_t s);
-cudaError_t launch_compress_tiles(const CompressArgs &a, cudaStream_t s);
-cudaError_t launch_decompress_tiles(const DecompressArgs &a, cudaStream_t s);
+// one persistent launch over the tiles of n fields (1 <= n <= kMaxBatch)
+cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s);
+cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s);
 size_t bitmap_words_tiled(Dims d);
 cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
                                       const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,

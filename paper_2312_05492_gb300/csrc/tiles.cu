@@ -313,30 +313,51 @@ __device__ __forceinline__ void run_slab(float *box, const Sink &sk, const Slab 
 }
 
 // ------------------------------------------------------------ work list
-// A CTA's sequence of (item, slab): items blockIdx.x, +gridDim.x, ...; each
-// item is a run of up to f.run consecutive slabs of one column.
-struct Cursor {
-    int item, c, c_first, c_last;
+// Work items of all fields of a batch are numbered consecutively (field 0's
+// items first).  A CTA takes items blockIdx.x, +gridDim.x, ...; an item is a
+// run of up to f.run consecutive slabs of one column of one field.
+template <typename FieldT>
+struct BatchView {
+    const FieldT *fld;
+    int n, items;
 };
 
-__device__ __forceinline__ bool cursor_start(Cursor &cu, const Field &f, int item)
+struct Cursor {
+    int item, fi, c, c_first, c_last;
+};
+
+template <bool MULTI, typename FieldT>
+__device__ __forceinline__ bool cursor_start(Cursor &cu, const BatchView<FieldT> &b, int item)
 {
     cu.item = item;
-    if (item >= f.items) return false;
-    const int run_id = item / f.cols;
+    if (item >= b.items) return false;
+    int fi = 0;
+    if (MULTI)
+        while (fi + 1 < b.n && b.fld[fi + 1].item0 <= item) ++fi;
+    cu.fi = fi;
+    const Field &f = b.fld[fi].f;
+    const int run_id = (item - b.fld[fi].item0) / f.cols;
     cu.c_first = run_id * f.run;
     cu.c_last = min(cu.c_first + f.run, f.slabs) - 1;
     cu.c = cu.c_first;
     return true;
 }
 
-__device__ __forceinline__ bool cursor_next(Cursor &cu, const Field &f)
+template <bool MULTI, typename FieldT>
+__device__ __forceinline__ bool cursor_next(Cursor &cu, const BatchView<FieldT> &b)
 {
     if (cu.c < cu.c_last) {
         ++cu.c;
         return true;
     }
-    return cursor_start(cu, f, cu.item + gridDim.x);
+    return cursor_start<MULTI>(cu, b, cu.item + gridDim.x);
+}
+
+template <bool MULTI, typename FieldT>
+__device__ __forceinline__ void slab_of(Slab &s, const Cursor &cu, const BatchView<FieldT> &b)
+{
+    const FieldT &F = b.fld[MULTI ? cu.fi : 0];
+    slab_setup(s, F.f, cu.item - F.item0, cu.c, cu.c_first, cu.c_last);
 }
 
 // Bring the 9 x 17 x XP (or KP) input box of a slab into the landing buffer:
@@ -375,7 +396,8 @@ __device__ __forceinline__ void issue_land(T *land, const T *__restrict__ src, c
     cp_async_commit();
 }
 
-// Returns false if the landing transfer did not complete in time.
+// Wait for the landing transfer; false if it did not complete in time.
+// The caller follows with a block barrier before reading the buffer.
 __device__ __forceinline__ bool wait_land(bool use_tma, uint64_t *bar, uint32_t &phase)
 {
     if (use_tma) {
@@ -388,8 +410,64 @@ __device__ __forceinline__ bool wait_land(bool use_tma, uint64_t *bar, uint32_t 
 }
 
 // ------------------------------------------------------------ compression
-__global__ void __launch_bounds__(NT) k_compress(CompressArgs a, Field f, const __grid_constant__ CUtensorMap xmap,
-                                                 int use_tma)
+struct CField {
+    CompressArgs a;
+    Field f;
+    int item0;    // first batch item of this field
+    int use_tma;  // input rows described by map[] (else cp.async path)
+};
+
+struct CBatch {
+    CUtensorMap map[kMaxBatch];
+    CField fld[kMaxBatch];
+    int n, items;
+};
+
+// Per-field values of the compression write-out, re-read when the field changes.
+struct CWrite {
+    int R, bins, Ay, Ax, WX;
+    bool smem_hist, vec_codes;
+};
+
+__device__ __forceinline__ CWrite cwrite_of(const CField &F)
+{
+    CWrite w;
+    w.R = F.a.radius;
+    w.bins = 2 * w.R;
+    w.smem_hist = F.a.hist != nullptr && w.bins <= HIST_SMEM_BINS;
+    w.Ay = (F.f.n[1] - 1) / 8 + 1;
+    w.Ax = (F.f.n[2] - 1) / 8 + 1;
+    w.WX = (F.f.n[2] + 31) / 32;
+    w.vec_codes = F.a.vec_codes;
+    return w;
+}
+
+// Add the CTA's histogram counts of one field to its global bins and clear them.
+__device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uint32_t *hist_s, uint32_t &central)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) central += __shfl_xor_sync(0xffffffffu, central, off);
+    __syncthreads();
+    if (F.a.hist && lane == 0 && central) {
+        if (w.smem_hist) atomicAdd(&hist_s[w.R], central);
+        else atomicAdd(&F.a.hist[w.R], central);
+    }
+    central = 0;
+    __syncthreads();
+    if (w.smem_hist) {
+        for (int i = threadIdx.x; i < w.bins; i += NT) {
+            const uint32_t h = hist_s[i];
+            if (h) atomicAdd(&F.a.hist[i], h);
+        }
+    }
+    for (int i = threadIdx.x; i < HIST_SMEM_BINS; i += NT) hist_s[i] = 0u;
+    __syncthreads();
+}
+
+// MULTI = false: a single field (index 0 everywhere, resolved at compile time).
+template <bool MULTI>
+__global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch B)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Levels lv;
@@ -399,171 +477,180 @@ __global__ void __launch_bounds__(NT) k_compress(CompressArgs a, Field f, const 
     uint16_t *stage = reinterpret_cast<uint16_t *>(smem + C_STAGE);
     uint32_t *hist_s = reinterpret_cast<uint32_t *>(smem + C_HIST);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C_BAR);
+    const BatchView<CField> bv{B.fld, B.n, B.items};
 
-    const int R = a.hdr->cfg.radius;
-    const int bins = 2 * R;
-    const bool smem_hist = a.hist != nullptr && bins <= HIST_SMEM_BINS;
     if (threadIdx.x == 0) {
-        load_levels(lv, a.hdr);
         abort_flag = 0;
         mbar_init(bar, 1);
         fence_barrier_init();
     }
-    if (smem_hist)
-        for (int i = threadIdx.x; i < bins; i += NT) hist_s[i] = 0u;
+    for (int i = threadIdx.x; i < HIST_SMEM_BINS; i += NT) hist_s[i] = 0u;
     __syncthreads();
 
     uint32_t central = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Ay = (f.n[1] - 1) / 8 + 1, Ax = (f.n[2] - 1) / 8 + 1;
-    const int WX = (f.n[2] + 31) / 32;
-    const uint32_t RR = (uint32_t)R | ((uint32_t)R << 16);
-    const bool vec_codes = a.vec_codes;
     uint32_t phase = 0;
+    const Sink sk{stage, nullptr};
 
     Cursor cu;
-    if (cursor_start(cu, f, blockIdx.x)) {
-        Slab sl;
-        slab_setup(sl, f, cu.item, cu.c, cu.c_first, cu.c_last);
-        issue_land<float, XP>(land, a.x, &xmap, use_tma, bar, f, sl);
-        const Sink sk{stage, nullptr};
-        for (;;) {
-            Cursor nx = cu;
-            const bool has_next = cursor_next(nx, f);
-            Slab sn = sl;
-            if (has_next) slab_setup(sn, f, nx.item, nx.c, nx.c_first, nx.c_last);
+    if (!cursor_start<MULTI>(cu, bv, blockIdx.x)) return;
+    Slab sl;
+    slab_of<MULTI>(sl, cu, bv);
+    int lv_field = -1;
+    {
+        const int fi = MULTI ? cu.fi : 0;
+        issue_land<float, XP>(land, B.fld[fi].a.x, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f, sl);
+    }
+    for (;;) {
+        const int fi = MULTI ? cu.fi : 0;
+        const CField &F = B.fld[fi];
+        const Field &f = F.f;
+        Cursor nx = cu;
+        const bool has_next = cursor_next<MULTI>(nx, bv);
+        Slab sn = sl;
+        if (has_next) slab_of<MULTI>(sn, nx, bv);
+        if (threadIdx.x == 0 && lv_field != fi) load_levels(lv, F.a.hdr);
+        lv_field = fi;
 
-            // ---- landed input -> compute box (planes 0..8, or 1..8 when carried)
-            if (!wait_land(use_tma, bar, phase)) abort_flag = 1;
-            if (!use_tma) __syncthreads();
-            {
-                const int pz0 = sl.carried ? 1 : 0;
-                const int nitem = (EZ - pz0) * EY * 9;  // 9 groups of 4 floats per row (x 0..35)
-                for (int i = threadIdx.x; i < nitem; i += NT) {
-                    const int row = pz0 * EY + i / 9, q = i % 9;
-                    const float4 v = *reinterpret_cast<const float4 *>(land + row * XP + 4 * q);
-                    float *d = box + row * EX + 4 * q;
-                    d[0] = v.x;
-                    if (q < 8) {
-                        d[1] = v.y;
-                        d[2] = v.z;
-                        d[3] = v.w;
-                    }
+        // ---- landed input -> compute box (planes 0..8, or 1..8 when carried)
+        if (!wait_land(F.use_tma, bar, phase)) abort_flag = 1;
+        if (!F.use_tma) __syncthreads();  // cp.async copies of all threads visible
+        {
+            const int pz0 = sl.carried ? 1 : 0;
+            const int nitem = (EZ - pz0) * EY * 9;  // 9 groups of 4 floats per row (x 0..35)
+            for (int i = threadIdx.x; i < nitem; i += NT) {
+                const int row = pz0 * EY + i / 9, q = i % 9;
+                const float4 v = *reinterpret_cast<const float4 *>(land + row * XP + 4 * q);
+                float *d = box + row * EX + 4 * q;
+                d[0] = v.x;
+                if (q < 8) {
+                    d[1] = v.y;
+                    d[2] = v.z;
+                    d[3] = v.w;
                 }
             }
-            __syncthreads();  // box ready, landing buffer free
-            if (abort_flag) break;
-            if (has_next) issue_land<float, XP>(land, a.x, &xmap, use_tma, bar, f, sn);
+        }
+        __syncthreads();  // box and levels ready, landing buffer free
+        if (abort_flag) break;
+        if (has_next) {
+            const int nfi = MULTI ? nx.fi : 0;
+            const CField &N = B.fld[nfi];
+            issue_land<float, XP>(land, N.a.x, &B.map[nfi], N.use_tma, bar, N.f, sn);
+        }
 
-            run_slab<true>(box, sk, sl, f, lv);  // ends with a barrier
+        run_slab<true>(box, sk, sl, f, lv);  // ends with a barrier
 
-            // ---- owned planes: codes (16-byte stores), anchors, histogram, bitmap words.
-            // A warp takes 8 consecutive rows of one plane, 4 lanes x 8 codes per row.
-            const int nzp = min(EZ, f.n[0] - sl.g0[0]);
-            const int hi = min(sl.own_hi, nzp - 1);
-            const int rows = (hi - sl.own_lo + 1) * OY;
-            const int sub = lane & 3;
-            for (int base = warp * 8; base < rows; base += NWARP * 8) {
-                const int row = base + (lane >> 2);
-                const int pz = sl.own_lo + row / OY, y = row % OY;
-                const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y;
-                const int gx = sl.g0[2] + 8 * sub;
-                const bool rin = gy < f.n[1];
-                const int nvalid = rin ? min(8, f.n[2] - gx) : 0;  // in-field codes of this lane
-                const uint32_t *srow = reinterpret_cast<const uint32_t *>(stage + pz * STAGE_PLANE + y * CP + 8 * sub);
-                uint32_t w[4];
+        // ---- owned planes: codes (16-byte stores), anchors, histogram, bitmap words.
+        // A warp takes 8 consecutive rows of one plane, 4 lanes x 8 codes per row.
+        const CWrite cw = cwrite_of(F);
+        const uint32_t RR = (uint32_t)cw.R | ((uint32_t)cw.R << 16);
+        const int nzp = min(EZ, f.n[0] - sl.g0[0]);
+        const int hi = min(sl.own_hi, nzp - 1);
+        const int rows = (hi - sl.own_lo + 1) * OY;
+        const int sub = lane & 3;
+        for (int base = warp * 8; base < rows; base += NWARP * 8) {
+            const int row = base + (lane >> 2);
+            const int pz = sl.own_lo + row / OY, y = row % OY;
+            const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y;
+            const int gx = sl.g0[2] + 8 * sub;
+            const bool rin = gy < f.n[1];
+            const int nvalid = rin ? min(8, f.n[2] - gx) : 0;  // in-field codes of this lane
+            const uint32_t *srow = reinterpret_cast<const uint32_t *>(stage + pz * STAGE_PLANE + y * CP + 8 * sub);
+            uint32_t w[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w[j] = srow[j];
-                const size_t gi = ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
-                if (nvalid > 0 && ((pz | y) & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
-                    w[0] = (w[0] & 0xffff0000u) | (uint32_t)R;
-                    a.anchors[((size_t)(gz / 8) * Ay + gy / 8) * Ax + gx / 8] = box[pz * PLANE + y * EX + 8 * sub];
-                }
-                uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
-                if (nvalid == 8) {
-                    if (vec_codes) {
-                        *reinterpret_cast<uint4 *>(a.codes + gi) = make_uint4(w[0], w[1], w[2], w[3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            a.codes[gi + 2 * j] = (uint16_t)(w[j] & 0xffffu);
-                            a.codes[gi + 2 * j + 1] = (uint16_t)(w[j] >> 16);
-                        }
-                    }
+            for (int j = 0; j < 4; ++j) w[j] = srow[j];
+            const size_t gi = ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
+            if (nvalid > 0 && ((pz | y) & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
+                w[0] = (w[0] & 0xffff0000u) | (uint32_t)cw.R;
+                F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] =
+                    box[pz * PLANE + y * EX + 8 * sub];
+            }
+            uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
+            if (nvalid == 8) {
+                if (cw.vec_codes) {
+                    *reinterpret_cast<uint4 *>(F.a.codes + gi) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const uint32_t z = __vcmpeq2(w[j], 0u);
-                        zmask |= ((z & 1u) | ((z >> 15) & 2u)) << (2 * j);
-                        central += (uint32_t)__popc(__vcmpeq2(w[j], RR)) >> 4;
-                        const uint32_t lo = w[j] & 0xffffu, hi16 = w[j] >> 16;
-                        if (lo != (uint32_t)R && lo < (uint32_t)bins) {
-                            if (smem_hist) atomicAdd(&hist_s[lo], 1u);
-                            else if (a.hist) atomicAdd(&a.hist[lo], 1u);
-                        }
-                        if (hi16 != (uint32_t)R && hi16 < (uint32_t)bins) {
-                            if (smem_hist) atomicAdd(&hist_s[hi16], 1u);
-                            else if (a.hist) atomicAdd(&a.hist[hi16], 1u);
-                        }
-                    }
-                } else {
-                    for (int j = 0; j < nvalid; ++j) {
-                        const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-                        a.codes[gi + j] = (uint16_t)c;
-                        if (c == 0u) zmask |= 1u << j;
-                        if (c == (uint32_t)R) ++central;
-                        else if (c < (uint32_t)bins) {
-                            if (smem_hist) atomicAdd(&hist_s[c], 1u);
-                            else if (a.hist) atomicAdd(&a.hist[c], 1u);
-                        }
+                        F.a.codes[gi + 2 * j] = (uint16_t)(w[j] & 0xffffu);
+                        F.a.codes[gi + 2 * j + 1] = (uint16_t)(w[j] >> 16);
                     }
                 }
-                // the 4 lanes of a row assemble its 32-bit outlier word
-                uint32_t word = zmask << (8 * sub);
-                word |= __shfl_xor_sync(0xffffffffu, word, 1);
-                word |= __shfl_xor_sync(0xffffffffu, word, 2);
-                if (sub == 0 && rin) {
-                    // tile-major bitmap: a slab's words are contiguous per plane
-                    a.bitmap[((size_t)sl.col * f.n[0] + gz) * OY + y] = word;
-                    if (word) {
-                        const int64_t gw = ((int64_t)gz * f.n[1] + gy) * WX + sl.g0[2] / 32;  // global order
-                        atomicAdd(&a.blockcnt[gw / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
-                    }
-                }
-            }
-            // ---- carry plane 8 into plane 0 of the next slab of the same run
-            if (has_next && nx.item == cu.item) {
-                __syncthreads();  // write-out finished reading plane 8 anchors
-                for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
-            }
-            __syncthreads();  // box and staging free for the next slab
-            if (!has_next) break;
-            cu = nx;
-            sl = sn;
-        }
-        if (!use_tma) cp_async_wait_all();
-        if (abort_flag && threadIdx.x == 0) atomicOr(&a.hdr->status, INTERP_STATUS_TIMEOUT);
-    }
-
-    if (a.hist) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) central += __shfl_xor_sync(0xffffffffu, central, off);
-        if (lane == 0 && central) {
-            if (smem_hist) atomicAdd(&hist_s[R], central);
-            else atomicAdd(&a.hist[R], central);
-        }
-        if (smem_hist) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < bins; i += NT) {
-                const uint32_t h = hist_s[i];
-                if (h) atomicAdd(&a.hist[i], h);
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t z = __vcmpeq2(w[j], 0u);
+                    zmask |= ((z & 1u) | ((z >> 15) & 2u)) << (2 * j);
+                    central += (uint32_t)__popc(__vcmpeq2(w[j], RR)) >> 4;
+                    const uint32_t lo = w[j] & 0xffffu, hi16 = w[j] >> 16;
+                    if (lo != (uint32_t)cw.R && lo < (uint32_t)cw.bins) {
+                        if (cw.smem_hist) atomicAdd(&hist_s[lo], 1u);
+                        else if (F.a.hist) atomicAdd(&F.a.hist[lo], 1u);
+                    }
+                    if (hi16 != (uint32_t)cw.R && hi16 < (uint32_t)cw.bins) {
+                        if (cw.smem_hist) atomicAdd(&hist_s[hi16], 1u);
+                        else if (F.a.hist) atomicAdd(&F.a.hist[hi16], 1u);
+                    }
+                }
+            } else {
+                for (int j = 0; j < nvalid; ++j) {
+                    const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                    F.a.codes[gi + j] = (uint16_t)c;
+                    if (c == 0u) zmask |= 1u << j;
+                    if (c == (uint32_t)cw.R) ++central;
+                    else if (c < (uint32_t)cw.bins) {
+                        if (cw.smem_hist) atomicAdd(&hist_s[c], 1u);
+                        else if (F.a.hist) atomicAdd(&F.a.hist[c], 1u);
+                    }
+                }
+            }
+            // the 4 lanes of a row assemble its 32-bit outlier word
+            uint32_t word = zmask << (8 * sub);
+            word |= __shfl_xor_sync(0xffffffffu, word, 1);
+            word |= __shfl_xor_sync(0xffffffffu, word, 2);
+            if (sub == 0 && rin) {
+                // tile-major bitmap: a slab's words are contiguous per plane
+                F.a.bitmap[((size_t)sl.col * f.n[0] + gz) * OY + y] = word;
+                if (word) {
+                    const int64_t gw = ((int64_t)gz * f.n[1] + gy) * cw.WX + sl.g0[2] / 32;  // ascending order
+                    atomicAdd(&F.a.blockcnt[gw / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
+                }
             }
         }
+        // ---- carry plane 8 into plane 0 of the next slab of the same run
+        if (has_next && nx.item == cu.item) {
+            __syncthreads();  // write-out finished reading plane 8 anchors
+            for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
+        }
+        __syncthreads();  // box and staging free for the next slab
+        if (!has_next || (MULTI && nx.fi != cu.fi)) flush_hist(F, cw, hist_s, central);  // field done on this CTA
+        if (!has_next) break;
+        cu = nx;
+        sl = sn;
     }
+    if (abort_flag) {
+        const int fi = MULTI ? cu.fi : 0;
+        if (threadIdx.x == 0) atomicOr(&B.fld[fi].a.hdr->status, INTERP_STATUS_TIMEOUT);
+        flush_hist(B.fld[fi], cwrite_of(B.fld[fi]), hist_s, central);
+    }
+    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------- decompression
-__global__ void __launch_bounds__(NT) k_decompress(DecompressArgs a, Field f, const __grid_constant__ CUtensorMap cmap,
-                                                   int use_tma)
+struct DField {
+    DecompressArgs a;
+    Field f;
+    int item0;
+    int use_tma;
+};
+
+struct DBatch {
+    CUtensorMap map[kMaxBatch];
+    DField fld[kMaxBatch];
+    int n, items;
+};
+
+template <bool MULTI>
+__global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatch B)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Levels lv;
@@ -572,33 +659,41 @@ __global__ void __launch_bounds__(NT) k_decompress(DecompressArgs a, Field f, co
     float *box = reinterpret_cast<float *>(smem + D_BOX);
     uint16_t *cbox = reinterpret_cast<uint16_t *>(smem + D_CBOX);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + D_BAR);
+    const BatchView<DField> bv{B.fld, B.n, B.items};
     if (threadIdx.x == 0) {
-        load_levels(lv, a.hdr);
         abort_flag = 0;
         mbar_init(bar, 1);
         fence_barrier_init();
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Ay = (f.n[1] - 1) / 8 + 1, Ax = (f.n[2] - 1) / 8 + 1;
-    const bool vec_x = a.vec_xrec;
     uint32_t phase = 0;
+    const Sink sk{nullptr, cbox};
 
     Cursor cu;
-    if (!cursor_start(cu, f, blockIdx.x)) return;
+    if (!cursor_start<MULTI>(cu, bv, blockIdx.x)) return;
     Slab sl;
-    slab_setup(sl, f, cu.item, cu.c, cu.c_first, cu.c_last);
-    issue_land<uint16_t, KP>(land, a.codes, &cmap, use_tma, bar, f, sl);
-    const Sink sk{nullptr, cbox};
+    slab_of<MULTI>(sl, cu, bv);
+    int lv_field = -1;
+    {
+        const int fi = MULTI ? cu.fi : 0;
+        issue_land<uint16_t, KP>(land, B.fld[fi].a.codes, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f, sl);
+    }
     for (;;) {
+        const int fi = MULTI ? cu.fi : 0;
+        const DField &F = B.fld[fi];
+        const Field &f = F.f;
+        const int Ay = (f.n[1] - 1) / 8 + 1, Ax = (f.n[2] - 1) / 8 + 1;
         Cursor nx = cu;
-        const bool has_next = cursor_next(nx, f);
+        const bool has_next = cursor_next<MULTI>(nx, bv);
         Slab sn = sl;
-        if (has_next) slab_setup(sn, f, nx.item, nx.c, nx.c_first, nx.c_last);
+        if (has_next) slab_of<MULTI>(sn, nx, bv);
+        if (threadIdx.x == 0 && lv_field != fi) load_levels(lv, F.a.hdr);
+        lv_field = fi;
 
         // ---- landed codes -> code box; outliers' stored values and anchors -> value box
-        if (!wait_land(use_tma, bar, phase)) abort_flag = 1;
-        if (!use_tma) __syncthreads();
+        if (!wait_land(F.use_tma, bar, phase)) abort_flag = 1;
+        __syncthreads();  // copies visible; the previous slab's box writes are done
         {
             const int pz0 = sl.carried ? 1 : 0;
             const int nzp = min(EZ, f.n[0] - sl.g0[0]);
@@ -624,7 +719,7 @@ __global__ void __launch_bounds__(NT) k_decompress(DecompressArgs a, Field f, co
                         if (((wv[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) {
                             const size_t g = ((size_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * f.n[2] + sl.g0[2] +
                                              8 * q + j;
-                            box[row * EX + 8 * q + j] = __ldg(a.xrec + g);
+                            box[row * EX + 8 * q + j] = __ldg(F.a.xrec + g);
                         }
                     }
                 }
@@ -635,12 +730,16 @@ __global__ void __launch_bounds__(NT) k_decompress(DecompressArgs a, Field f, co
                 const int pz = 8 * az, y = 8 * ay, x = 8 * ax;
                 if ((az == 0 && sl.carried) || pz >= nzp || y >= nyr || x >= nxc) continue;
                 const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gxx = sl.g0[2] + x;
-                box[pz * PLANE + y * EX + x] = __ldg(a.anchors + ((size_t)(gz / 8) * Ay + gy / 8) * Ax + gxx / 8);
+                box[pz * PLANE + y * EX + x] = __ldg(F.a.anchors + ((size_t)(gz / 8) * Ay + gy / 8) * Ax + gxx / 8);
             }
         }
-        __syncthreads();  // code box and anchors ready, landing buffer free
+        __syncthreads();  // code box, anchors and levels ready, landing buffer free
         if (abort_flag) break;
-        if (has_next) issue_land<uint16_t, KP>(land, a.codes, &cmap, use_tma, bar, f, sn);
+        if (has_next) {
+            const int nfi = MULTI ? nx.fi : 0;
+            const DField &N = B.fld[nfi];
+            issue_land<uint16_t, KP>(land, N.a.codes, &B.map[nfi], N.use_tma, bar, N.f, sn);
+        }
 
         run_slab<false>(box, sk, sl, f, lv);  // ends with a barrier
 
@@ -649,13 +748,14 @@ __global__ void __launch_bounds__(NT) k_decompress(DecompressArgs a, Field f, co
         const int hi = min(sl.own_hi, nzp - 1);
         const int rows = (hi - sl.own_lo + 1) * OY;
         const int sub = lane & 7;
+        const bool vec_x = F.a.vec_xrec;
         for (int base = warp * 4; base < rows; base += NWARP * 4) {
             const int row = base + (lane >> 3);
             const int pz = sl.own_lo + row / OY, y = row % OY;
             const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gx = sl.g0[2] + 4 * sub;
             if (gy >= f.n[1] || gx >= f.n[2]) continue;
             const float *s4 = box + pz * PLANE + y * EX + 4 * sub;
-            float *dst = a.xrec + ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
+            float *dst = F.a.xrec + ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
             if (vec_x && gx + 3 < f.n[2]) {
                 *reinterpret_cast<float4 *>(dst) = make_float4(s4[0], s4[1], s4[2], s4[3]);
             } else {
@@ -672,14 +772,15 @@ __global__ void __launch_bounds__(NT) k_decompress(DecompressArgs a, Field f, co
         cu = nx;
         sl = sn;
     }
-    if (!use_tma) cp_async_wait_all();
-    if (abort_flag && threadIdx.x == 0) atomicOr(&const_cast<interp_header *>(a.hdr)->status, INTERP_STATUS_TIMEOUT);
+    if (abort_flag && threadIdx.x == 0)
+        atomicOr(&const_cast<interp_header *>(B.fld[MULTI ? cu.fi : 0].a.hdr)->status, INTERP_STATUS_TIMEOUT);
+    cp_async_wait_all();
 }
 
 // ------------------------------------------------------------ host side
 constexpr int kMaxDevices = 64;
-int compress_grid[kMaxDevices];
-int decompress_grid[kMaxDevices];
+int compress_grid[kMaxDevices], compress_grid_multi[kMaxDevices];
+int decompress_grid[kMaxDevices], decompress_grid_multi[kMaxDevices];
 
 // Opt in to the kernel's dynamic shared memory and size the persistent grid
 // (resident CTAs per SM x SMs), once per device.
@@ -704,9 +805,7 @@ cudaError_t prepare(K kernel, size_t smem, int *cache, int &grid)
     return cudaSuccess;
 }
 
-// Split the slabs of every column into runs so that the busiest CTA of the
-// persistent grid has the least work (each run start recomputes one plane).
-Field plan(Dims d, int grid)
+Field field_of(Dims d)
 {
     Field f;
     f.n[0] = d.nz;
@@ -715,20 +814,39 @@ Field plan(Dims d, int grid)
     f.cols_x = (d.nx + OX - 1) / OX;
     f.cols = f.cols_x * ((d.ny + OY - 1) / OY);
     f.slabs = d.nz > 1 ? (d.nz - 1 + 7) / 8 : 1;
-    int best_run = f.slabs;
+    f.run = f.slabs;
+    f.items = f.cols;
+    return f;
+}
+
+// Split the slabs of every column of every field into runs of one common
+// length so that the busiest CTA of the persistent grid has the least work
+// (each run start recomputes one plane).
+void plan_runs(Field *fs, int n, int grid)
+{
+    int max_slabs = 1;
+    for (int i = 0; i < n; ++i) max_slabs = max(max_slabs, fs[i].slabs);
+    int best_run = max_slabs;
     double best = 1e300;
-    for (int run = 1; run <= f.slabs; ++run) {
-        const long long items = (long long)f.cols * ((f.slabs + run - 1) / run);
+    for (int run = 1; run <= max_slabs; ++run) {
+        long long items = 0, work = 0;
+        for (int i = 0; i < n; ++i) {
+            items += (long long)fs[i].cols * ((fs[i].slabs + run - 1) / run);
+            work += (long long)fs[i].cols * fs[i].slabs;
+        }
         const long long per_cta = (items + grid - 1) / grid;
+        // a CTA's time ~ its items x the run length, plus a recomputed plane per item
         const double cost = (double)per_cta * (run + 0.15);
+        (void)work;
         if (cost < best - 1e-9) {
             best = cost;
             best_run = run;
         }
     }
-    f.run = best_run;
-    f.items = f.cols * ((f.slabs + f.run - 1) / f.run);
-    return f;
+    for (int i = 0; i < n; ++i) {
+        fs[i].run = min(best_run, fs[i].slabs);
+        fs[i].items = fs[i].cols * ((fs[i].slabs + fs[i].run - 1) / fs[i].run);
+    }
 }
 
 }  // namespace
@@ -739,34 +857,64 @@ size_t bitmap_words_tiled(Dims d)
     return cols * (size_t)d.nz * OY;
 }
 
-cudaError_t launch_compress_tiles(const CompressArgs &a, cudaStream_t s)
+cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s)
 {
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     int grid = 0;
-    cudaError_t e = prepare(k_compress, kCompressSmem, compress_grid, grid);
+    cudaError_t e = n > 1 ? prepare(k_compress<true>, kCompressSmem, compress_grid_multi, grid)
+                          : prepare(k_compress<false>, kCompressSmem, compress_grid, grid);
     if (e != cudaSuccess) return e;
-    const Field f = plan(a.dims, grid);
-    if (f.items < grid) grid = f.items;
-    CUtensorMap map;
-    const uint32_t box[3] = {XP, EY, EZ};
-    const int use_tma = encode_tensor_map_3d(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.x, a.dims, box) ? 1 : 0;
-    if (!use_tma) std::memset(&map, 0, sizeof(map));
-    k_compress<<<grid, NT, kCompressSmem, s>>>(a, f, map, use_tma);
+    thread_local CBatch B;  // large parameter block, filled on the host
+    std::memset(&B, 0, sizeof(B));
+    Field fs[kMaxBatch];
+    for (int i = 0; i < n; ++i) fs[i] = field_of(args[i].dims);
+    plan_runs(fs, n, grid);
+    int items = 0;
+    for (int i = 0; i < n; ++i) {
+        B.fld[i].a = args[i];
+        B.fld[i].f = fs[i];
+        B.fld[i].item0 = items;
+        items += fs[i].items;
+        const uint32_t box[3] = {XP, EY, EZ};
+        B.fld[i].use_tma =
+            encode_tensor_map_3d(&B.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, args[i].x, args[i].dims, box) ? 1 : 0;
+    }
+    B.n = n;
+    B.items = items;
+    if (items < grid) grid = items;
+    if (n > 1) k_compress<true><<<grid, NT, kCompressSmem, s>>>(B);
+    else k_compress<false><<<grid, NT, kCompressSmem, s>>>(B);
     return cudaGetLastError();
 }
 
-cudaError_t launch_decompress_tiles(const DecompressArgs &a, cudaStream_t s)
+cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s)
 {
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     int grid = 0;
-    cudaError_t e = prepare(k_decompress, kDecompressSmem, decompress_grid, grid);
+    cudaError_t e = n > 1 ? prepare(k_decompress<true>, kDecompressSmem, decompress_grid_multi, grid)
+                          : prepare(k_decompress<false>, kDecompressSmem, decompress_grid, grid);
     if (e != cudaSuccess) return e;
-    const Field f = plan(a.dims, grid);
-    if (f.items < grid) grid = f.items;
-    CUtensorMap map;
-    const uint32_t box[3] = {KP, EY, EZ};
-    const int use_tma =
-        encode_tensor_map_3d(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, a.codes, a.dims, box) ? 1 : 0;
-    if (!use_tma) std::memset(&map, 0, sizeof(map));
-    k_decompress<<<grid, NT, kDecompressSmem, s>>>(a, f, map, use_tma);
+    thread_local DBatch B;
+    std::memset(&B, 0, sizeof(B));
+    Field fs[kMaxBatch];
+    for (int i = 0; i < n; ++i) fs[i] = field_of(args[i].dims);
+    plan_runs(fs, n, grid);
+    int items = 0;
+    for (int i = 0; i < n; ++i) {
+        B.fld[i].a = args[i];
+        B.fld[i].f = fs[i];
+        B.fld[i].item0 = items;
+        items += fs[i].items;
+        const uint32_t box[3] = {KP, EY, EZ};
+        B.fld[i].use_tma =
+            encode_tensor_map_3d(&B.map[i], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, args[i].codes, args[i].dims, box) ? 1
+                                                                                                                   : 0;
+    }
+    B.n = n;
+    B.items = items;
+    if (items < grid) grid = items;
+    if (n > 1) k_decompress<true><<<grid, NT, kDecompressSmem, s>>>(B);
+    else k_decompress<false><<<grid, NT, kDecompressSmem, s>>>(B);
     return cudaGetLastError();
 }
 

@@ -24,7 +24,8 @@ STATUS_CAPACITY, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 
 FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress", "interp_decompress",
              "qcode_histogram", "interp_autotune", "interp_timing_enable", "interp_timing_read",
-             "interp_compress_noalloc", "interp_noalloc_scratch_bytes", "interp_status_string")
+             "interp_compress_noalloc", "interp_noalloc_scratch_bytes", "interp_compress_batched",
+             "interp_decompress_batched", "interp_status_string")
 
 # kernels each call launches (memsets excluded): compress = [profile] + range or
 # header + tiles + outlier scan + outlier write; decompress = scatter + tiles
@@ -49,6 +50,21 @@ class interp_header(ctypes.Structure):
                 ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("profile", ctypes.c_double * 18)]
 
 
+class interp_compress_item(ctypes.Structure):
+    _fields_ = [("d_x", ctypes.c_void_p), ("dims", ctypes.c_int64 * 3), ("eb", ctypes.c_double),
+                ("cfg", interp_config), ("d_anchors", ctypes.c_void_p), ("d_codes", ctypes.c_void_p),
+                ("d_out_idx", ctypes.c_void_p), ("d_out_val", ctypes.c_void_p), ("out_capacity", ctypes.c_uint64),
+                ("d_hist", ctypes.c_void_p), ("d_hdr", ctypes.c_void_p), ("d_ws", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t)]
+
+
+class interp_decompress_item(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int64 * 3), ("d_hdr", ctypes.c_void_p), ("d_anchors", ctypes.c_void_p),
+                ("d_codes", ctypes.c_void_p), ("d_out_idx", ctypes.c_void_p), ("d_out_val", ctypes.c_void_p),
+                ("out_capacity", ctypes.c_uint64), ("d_xrec", ctypes.c_void_p)]
+
+
+MAX_BATCH = 16
 HEADER_BYTES = ctypes.sizeof(interp_header)
 _lib = None
 
@@ -88,6 +104,10 @@ def load() -> ctypes.CDLL:
     lib.interp_compress_noalloc.argtypes = [P, dims_t, ctypes.c_double, cfg_p, P, P, P, P, u64, P, P, P]
     lib.interp_noalloc_scratch_bytes.restype = ctypes.c_size_t
     lib.interp_noalloc_scratch_bytes.argtypes = []
+    lib.interp_compress_batched.restype = ctypes.c_int
+    lib.interp_compress_batched.argtypes = [ctypes.POINTER(interp_compress_item), ctypes.c_int, P]
+    lib.interp_decompress_batched.restype = ctypes.c_int
+    lib.interp_decompress_batched.argtypes = [ctypes.POINTER(interp_decompress_item), ctypes.c_int, P]
     lib.interp_status_string.restype = ctypes.c_char_p
     lib.interp_status_string.argtypes = [ctypes.c_int]
     _lib = lib
@@ -161,6 +181,16 @@ def interp_compress_noalloc(d_x, dims, eb, cfg, d_anchors, d_codes, d_out_idx, d
 
 def interp_noalloc_scratch_bytes() -> int:
     return int(load().interp_noalloc_scratch_bytes())
+
+
+def interp_compress_batched(items, stream) -> int:
+    arr = (interp_compress_item * len(items))(*items)
+    return load().interp_compress_batched(arr, len(items), stream)
+
+
+def interp_decompress_batched(items, stream) -> int:
+    arr = (interp_decompress_item * len(items))(*items)
+    return load().interp_decompress_batched(arr, len(items), stream)
 
 
 def interp_status_string(rc: int) -> str:
@@ -347,3 +377,72 @@ def autotune(x: torch.Tensor, radius: int = 512, stream=None):
     cfg = Config(dim_order=tuple(c.dim_order), level_kind=tuple(c.level_kind), cubic_kind=tuple(c.cubic_kind),
                  radius=radius)
     return cfg, [float(v) for v in prof]
+
+
+# ------------------------------------------------------------ batched torch API
+def compress_item(x: torch.Tensor, eb: float, cfg: Config, bufs: dict, ws: torch.Tensor) -> interp_compress_item:
+    it = interp_compress_item()
+    it.d_x = _ptr(x)
+    it.dims[:] = [int(d) for d in x.shape]
+    it.eb = float(eb)
+    it.cfg = cfg.to_c()
+    it.d_anchors = _ptr(bufs["anchors"])
+    it.d_codes = _ptr(bufs["codes"])
+    it.d_out_idx = _ptr(bufs["out_idx"])
+    it.d_out_val = _ptr(bufs["out_val"])
+    it.out_capacity = int(bufs["capacity"])
+    it.d_hist = _ptr(bufs["hist"])
+    it.d_hdr = _ptr(bufs["header"])
+    it.d_ws = _ptr(ws)
+    it.ws_bytes = int(ws.numel())
+    return it
+
+
+def decompress_item(cf: CompressedField, out: torch.Tensor) -> interp_decompress_item:
+    it = interp_decompress_item()
+    it.dims[:] = [int(d) for d in cf.dims]
+    it.d_hdr = _ptr(cf.header)
+    it.d_anchors = _ptr(cf.anchors)
+    it.d_codes = _ptr(cf.codes)
+    it.d_out_idx = _ptr(cf.out_idx)
+    it.d_out_val = _ptr(cf.out_val)
+    it.out_capacity = int(cf.capacity)
+    it.d_xrec = _ptr(out)
+    return it
+
+
+class Batch:
+    """Preallocated buffers for compressing / decompressing a fixed set of fields
+    together: one persistent tile launch per call for all fields.  Reusable, and
+    capturable into a CUDA graph once it has run once (no host synchronisation)."""
+
+    def __init__(self, xs, ebs, cfgs, capacities=None, hist=True):
+        if not 1 <= len(xs) <= MAX_BATCH:
+            raise InterpError(f"a batch holds 1..{MAX_BATCH} fields")
+        for x in xs:
+            _check_field(x)
+        self.xs = list(xs)
+        self.ebs = [float(e) for e in ebs]
+        self.cfgs = list(cfgs)
+        caps = capacities or [None] * len(xs)
+        self.bufs = [allocate(tuple(x.shape), c, x.device, capacity=cap, hist=hist)
+                     for x, c, cap in zip(self.xs, self.cfgs, caps)]
+        self.ws = [torch.empty(max(1, interp_workspace_bytes(tuple(x.shape), c.to_c())), dtype=torch.uint8,
+                               device=x.device) for x, c in zip(self.xs, self.cfgs)]
+        self.fields = [CompressedField(tuple(x.shape), c, b["header"], b["anchors"], b["codes"], b["out_idx"],
+                                       b["out_val"], b["hist"], b["capacity"])
+                       for x, c, b in zip(self.xs, self.cfgs, self.bufs)]
+        self.outs = [torch.empty_like(x) for x in self.xs]
+        self._citems = [compress_item(x, e, c, b, w) for x, e, c, b, w in
+                        zip(self.xs, self.ebs, self.cfgs, self.bufs, self.ws)]
+        self._ditems = [decompress_item(cf, o) for cf, o in zip(self.fields, self.outs)]
+
+    def compress(self, stream=None):
+        _check(interp_compress_batched(self._citems, _stream_ptr(stream)), "interp_compress_batched")
+
+    def decompress(self, stream=None):
+        _check(interp_decompress_batched(self._ditems, _stream_ptr(stream)), "interp_decompress_batched")
+
+    def round_trip(self, stream=None):
+        self.compress(stream)
+        self.decompress(stream)

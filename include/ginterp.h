@@ -172,6 +172,21 @@ int interp_decompress_batched(const interp_decompress_item *h_items, int n, inte
 int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_t *d_hist,
                     interp_stream_t stream);
 
+/* Eq. 1 (Sec. IV-B.2): the level-bound reduction factor alpha = A(eps) for a relative
+ * bound eps, the value interp_compress uses in relative mode when cfg->alpha <= 0
+ * (piecewise linear between 1 at eps <= 1e-5 and 2 at eps >= 1e-1).  Host-only, pure. */
+double interp_alpha(double eps);
+
+/* Value range of a field (Sec. IV-B.1: a relative bound is scaled by the value range):
+ * writes {vmin, vmax} over the finite values of d_x (N = dims product floats,
+ * contiguous) to d_range (2 floats, device); {0, 0} when no value is finite.  This is
+ * the reduction interp_compress runs in relative mode; a caller that splits one field
+ * across GPUs reduces the per-part ranges and passes eps * (vmax - vmin) as an absolute
+ * bound.  d_ws: any workspace sized by interp_workspace_bytes() for the same dims.
+ * Stream-ordered, no synchronisation; errors as interp_compress. */
+int interp_value_range(const float *d_x, const int64_t dims[3], float *d_range, void *d_ws, size_t ws_bytes,
+                       interp_stream_t stream);
+
 /* Sampling profile and decision (Sec. IV-B.1 data profiling, Sec. IV-B.2 auto-tuning):
  * fills h_cfg->dim_order, cubic_kind and level_kind from the 4x4x4 sample profile of
  * d_x and writes the 18 profile sums to h_profile (may be NULL).  Uses 512 bytes of

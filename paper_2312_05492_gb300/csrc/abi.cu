@@ -259,6 +259,25 @@ int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_
     return cuda_status(e);
 }
 
+double interp_alpha(double eps) { return alpha_of_eps(eps); }
+
+int interp_value_range(const float *d_x, const int64_t dims[3], float *d_range, void *d_ws, size_t ws_bytes,
+                       interp_stream_t stream)
+{
+    if (!dims_ok(dims) || !d_x || !d_range || !d_ws) return INTERP_EINVAL;
+    if (ws_bytes < kCtrlBytes + gi::range_partials_bytes()) return INTERP_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char *ws = static_cast<unsigned char *>(d_ws);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(ws);
+    cudaError_t e = cudaMemsetAsync(ws, 0, kCtrlBytes, s);
+    if (e == cudaSuccess) {
+        interp_config unused{};
+        e = gi::launch_range(d_x, to_dims(dims), 0.0, unused, 1.0, nullptr, ws + kCtrlBytes, counter,
+                             gi::range_blocks(), s, d_range);
+    }
+    return cuda_status(e);
+}
+
 int interp_autotune(const float *d_x, const int64_t dims[3], interp_config *h_cfg, double *h_profile, void *d_ws,
                     size_t ws_bytes, interp_stream_t stream)
 {

@@ -24,7 +24,11 @@ namespace gi {
 #ifndef GI_TILE_THREADS
 #define GI_TILE_THREADS 256
 #endif
-constexpr int OY = 16, OX = 32;  // owned extent of a column
+#ifndef GI_TILE_ROWS
+#define GI_TILE_ROWS 16
+#endif
+constexpr int OY = GI_TILE_ROWS, OX = 32;  // owned extent of a column
+static_assert(OY % 8 == 0, "columns hold whole chunks");
 constexpr int TILE_THREADS = GI_TILE_THREADS;
 static_assert(OX == 32, "one outlier-bitmap word covers the 32 x-positions of an owned row");
 
@@ -132,7 +136,8 @@ cudaError_t launch_header_init(interp_header *hdr, Dims d, double eb, interp_con
                                cudaStream_t s);
 cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s);
 cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, double alpha, interp_header *hdr,
-                         void *partials, unsigned int *counter, int nblocks, cudaStream_t s);
+                         void *partials, unsigned int *counter, int nblocks, cudaStream_t s,
+                         float *out_range = nullptr);  // hdr == nullptr: write {vmin, vmax} to out_range
 // one persistent launch over the tiles of n fields (1 <= n <= kMaxBatch)
 cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s);
 cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s);

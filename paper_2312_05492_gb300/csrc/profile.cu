@@ -81,7 +81,7 @@ __device__ __forceinline__ void range_acc(float v, float &lo, float &hi, unsigne
 __global__ void __launch_bounds__(RANGE_THREADS) k_range(const float *__restrict__ x, unsigned long long n, int vec,
                                                         RangePartial *partials, unsigned int *counter,
                                                         interp_header *hdr, Dims d, double eb, interp_config cfg,
-                                                        double alpha)
+                                                        double alpha, float *out_range)
 {
     float lo = INFINITY, hi = -INFINITY;
     unsigned long long bad = 0;
@@ -169,7 +169,12 @@ __global__ void __launch_bounds__(RANGE_THREADS) k_range(const float *__restrict
             p.lo = 0.0f;
             p.hi = 0.0f;
         }
-        write_bounds(hdr, d, eb, cfg, alpha, p.lo, p.hi, p.nonfinite);
+        if (hdr) {
+            write_bounds(hdr, d, eb, cfg, alpha, p.lo, p.hi, p.nonfinite);
+        } else {
+            out_range[0] = p.lo;
+            out_range[1] = p.hi;
+        }
         *counter = 0u;  // ready for the next call on this workspace
     }
 }
@@ -293,13 +298,13 @@ cudaError_t launch_header_init(interp_header *hdr, Dims d, double eb, interp_con
 }
 
 cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, double alpha, interp_header *hdr,
-                         void *partials, unsigned int *counter, int nblocks, cudaStream_t s)
+                         void *partials, unsigned int *counter, int nblocks, cudaStream_t s, float *out_range)
 {
     const unsigned long long n = (unsigned long long)d.nz * d.ny * d.nx;
     const int vec = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
     if (nblocks > RANGE_MAX_BLOCKS) nblocks = RANGE_MAX_BLOCKS;
     k_range<<<nblocks, RANGE_THREADS, 0, s>>>(x, n, vec, reinterpret_cast<RangePartial *>(partials), counter, hdr, d,
-                                             eb, cfg, alpha);
+                                             eb, cfg, alpha, out_range);
     return cudaGetLastError();
 }
 

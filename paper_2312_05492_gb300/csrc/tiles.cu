@@ -79,8 +79,8 @@ constexpr size_t D_BOX = al16(D_LAND + sizeof(uint16_t) * KLAND);
 constexpr size_t D_CBOX = al16(D_BOX + sizeof(float) * BOXF);
 constexpr size_t D_BAR = al16(D_CBOX + sizeof(uint16_t) * CBOX);
 constexpr size_t kDecompressSmem = D_BAR + 16;
-// 4 compression CTAs per SM: dynamic + static (~128 B) + 1 KB reserved each, in 228 KB
-static_assert(4 * (kCompressSmem + 128 + 1024) <= 228 * 1024, "four compression CTAs per SM");
+// with 16-row columns, 4 compression CTAs fit an SM: dynamic + static (~128 B) + 1 KB reserved each
+static_assert(OY != 16 || 4 * (kCompressSmem + 128 + 1024) <= 228 * 1024, "four compression CTAs per SM");
 
 // ------------------------------------------------------------ cp.async (fallback path)
 __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
@@ -442,10 +442,24 @@ __device__ __forceinline__ CWrite cwrite_of(const CField &F)
     return w;
 }
 
+// Per-lane counters of the central code live in the spare padding word of
+// staging rows 0..31 (codes occupy 32 of each row's 34 half-words).
+__device__ __forceinline__ uint32_t *central_counter(uint16_t *stage, int lane)
+{
+    return reinterpret_cast<uint32_t *>(stage + lane * CP) + OX / 2;
+}
+
 // Add the CTA's histogram counts of one field to its global bins and clear them.
-__device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uint32_t *hist_s, uint32_t &central)
+__device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uint32_t *hist_s, uint32_t &central,
+                                           uint16_t *stage)
 {
     const int lane = threadIdx.x & 31;
+    __syncthreads();
+    if (threadIdx.x < 32) {  // fold the per-lane central counters into the register count
+        uint32_t *ctr = central_counter(stage, lane);
+        central += *ctr;
+        *ctr = 0u;
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) central += __shfl_xor_sync(0xffffffffu, central, off);
     __syncthreads();
@@ -485,12 +499,14 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
         fence_barrier_init();
     }
     for (int i = threadIdx.x; i < HIST_SMEM_BINS; i += NT) hist_s[i] = 0u;
+    if (threadIdx.x < 32) *central_counter(stage, threadIdx.x) = 0u;
     __syncthreads();
 
     uint32_t central = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t phase = 0;
     const Sink sk{stage, nullptr};
+    uint32_t *const lane_ctr = central_counter(stage, lane);
 
     Cursor cu;
     if (!cursor_start<MULTI>(cu, bv, blockIdx.x)) return;
@@ -543,7 +559,6 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
         // ---- owned planes: codes (16-byte stores), anchors, histogram, bitmap words.
         // A warp takes 8 consecutive rows of one plane, 4 lanes x 8 codes per row.
         const CWrite cw = cwrite_of(F);
-        const uint32_t RR = (uint32_t)cw.R | ((uint32_t)cw.R << 16);
         const int nzp = min(EZ, f.n[0] - sl.g0[0]);
         const int hi = min(sl.own_hi, nzp - 1);
         const int rows = (hi - sl.own_lo + 1) * OY;
@@ -565,42 +580,28 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
                 F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] =
                     box[pz * PLANE + y * EX + 8 * sub];
             }
-            uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
-            if (nvalid == 8) {
-                if (cw.vec_codes) {
-                    *reinterpret_cast<uint4 *>(F.a.codes + gi) = make_uint4(w[0], w[1], w[2], w[3]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        F.a.codes[gi + 2 * j] = (uint16_t)(w[j] & 0xffffu);
-                        F.a.codes[gi + 2 * j + 1] = (uint16_t)(w[j] >> 16);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t z = __vcmpeq2(w[j], 0u);
-                    zmask |= ((z & 1u) | ((z >> 15) & 2u)) << (2 * j);
-                    central += (uint32_t)__popc(__vcmpeq2(w[j], RR)) >> 4;
-                    const uint32_t lo = w[j] & 0xffffu, hi16 = w[j] >> 16;
-                    if (lo != (uint32_t)cw.R && lo < (uint32_t)cw.bins) {
-                        if (cw.smem_hist) atomicAdd(&hist_s[lo], 1u);
-                        else if (F.a.hist) atomicAdd(&F.a.hist[lo], 1u);
-                    }
-                    if (hi16 != (uint32_t)cw.R && hi16 < (uint32_t)cw.bins) {
-                        if (cw.smem_hist) atomicAdd(&hist_s[hi16], 1u);
-                        else if (F.a.hist) atomicAdd(&F.a.hist[hi16], 1u);
-                    }
-                }
+            // codes to global memory
+            if (nvalid == 8 && cw.vec_codes) {
+                *reinterpret_cast<uint4 *>(F.a.codes + gi) = make_uint4(w[0], w[1], w[2], w[3]);
             } else {
-                for (int j = 0; j < nvalid; ++j) {
-                    const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-                    F.a.codes[gi + j] = (uint16_t)c;
-                    if (c == 0u) zmask |= 1u << j;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < nvalid) F.a.codes[gi + j] = (uint16_t)(w[j >> 1] >> (16 * (j & 1)));
+            }
+            // outlier bits and histogram, one predicated atomic per code: the central
+            // code R (the most frequent one) goes to this lane's private counter
+            uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                const bool valid = j < nvalid;
+                zmask |= (uint32_t)(valid && c == 0u) << j;
+                if (cw.smem_hist) {
+                    uint32_t *bin = c == (uint32_t)cw.R ? lane_ctr : hist_s + c;
+                    if (valid && c < (uint32_t)cw.bins) atomicAdd(bin, 1u);
+                } else if (valid && F.a.hist && c < (uint32_t)cw.bins) {
                     if (c == (uint32_t)cw.R) ++central;
-                    else if (c < (uint32_t)cw.bins) {
-                        if (cw.smem_hist) atomicAdd(&hist_s[c], 1u);
-                        else if (F.a.hist) atomicAdd(&F.a.hist[c], 1u);
-                    }
+                    else atomicAdd(&F.a.hist[c], 1u);
                 }
             }
             // the 4 lanes of a row assemble its 32-bit outlier word
@@ -622,7 +623,7 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
             for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
         }
         __syncthreads();  // box and staging free for the next slab
-        if (!has_next || (MULTI && nx.fi != cu.fi)) flush_hist(F, cw, hist_s, central);  // field done on this CTA
+        if (!has_next || (MULTI && nx.fi != cu.fi)) flush_hist(F, cw, hist_s, central, stage);  // field done
         if (!has_next) break;
         cu = nx;
         sl = sn;
@@ -630,7 +631,7 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
     if (abort_flag) {
         const int fi = MULTI ? cu.fi : 0;
         if (threadIdx.x == 0) atomicOr(&B.fld[fi].a.hdr->status, INTERP_STATUS_TIMEOUT);
-        flush_hist(B.fld[fi], cwrite_of(B.fld[fi]), hist_s, central);
+        flush_hist(B.fld[fi], cwrite_of(B.fld[fi]), hist_s, central, stage);
     }
     cp_async_wait_all();
 }
@@ -725,8 +726,9 @@ __global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatc
                 }
             }
             // anchors of planes 8 and, when not carried, 0
-            for (int i = threadIdx.x; i < 2 * 3 * 5; i += NT) {
-                const int az = i / 15, ay = (i / 5) % 3, ax = i % 5;
+            constexpr int AYN = OY / 8 + 1, AXN = OX / 8 + 1;  // anchor rows / columns of the box
+            for (int i = threadIdx.x; i < 2 * AYN * AXN; i += NT) {
+                const int az = i / (AYN * AXN), ay = (i / AXN) % AYN, ax = i % AXN;
                 const int pz = 8 * az, y = 8 * ay, x = 8 * ax;
                 if ((az == 0 && sl.carried) || pz >= nzp || y >= nyr || x >= nxc) continue;
                 const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gxx = sl.g0[2] + x;

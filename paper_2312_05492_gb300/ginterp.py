@@ -25,7 +25,7 @@ STATUS_CAPACITY, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress", "interp_decompress",
              "qcode_histogram", "interp_autotune", "interp_timing_enable", "interp_timing_read",
              "interp_compress_noalloc", "interp_noalloc_scratch_bytes", "interp_compress_batched",
-             "interp_decompress_batched", "interp_status_string")
+             "interp_decompress_batched", "interp_status_string", "interp_alpha", "interp_value_range")
 
 # kernels each call launches (memsets excluded): compress = [profile] + range or
 # header + tiles + outlier scan + outlier write; decompress = scatter + tiles
@@ -94,6 +94,10 @@ def load() -> ctypes.CDLL:
     lib.interp_decompress.argtypes = [dims_t, P, P, P, P, P, u64, P, P]
     lib.qcode_histogram.restype = ctypes.c_int
     lib.qcode_histogram.argtypes = [P, u64, i32, P, P]
+    lib.interp_alpha.restype = ctypes.c_double
+    lib.interp_alpha.argtypes = [ctypes.c_double]
+    lib.interp_value_range.restype = ctypes.c_int
+    lib.interp_value_range.argtypes = [P, dims_t, P, P, ctypes.c_size_t, P]
     lib.interp_autotune.restype = ctypes.c_int
     lib.interp_autotune.argtypes = [P, dims_t, cfg_p, P, P, ctypes.c_size_t, P]
     lib.interp_timing_enable.restype = ctypes.c_int
@@ -152,6 +156,14 @@ def interp_decompress(dims, d_hdr, d_anchors, d_codes, d_out_idx, d_out_val, out
 
 def qcode_histogram(d_codes, n, radius, d_hist, stream) -> int:
     return load().qcode_histogram(d_codes, int(n), int(radius), d_hist, stream)
+
+
+def interp_alpha(eps: float) -> float:
+    return float(load().interp_alpha(float(eps)))
+
+
+def interp_value_range(d_x, dims, d_range, d_ws, ws_bytes, stream) -> int:
+    return load().interp_value_range(d_x, _dims(dims), d_range, d_ws, int(ws_bytes), stream)
 
 
 def interp_autotune(d_x, dims, cfg: interp_config, h_profile, d_ws, ws_bytes, stream) -> int:
@@ -362,6 +374,18 @@ def histogram(codes: torch.Tensor, radius: int, stream=None) -> torch.Tensor:
     rc = qcode_histogram(_ptr(codes), codes.numel(), radius, _ptr(hist), _stream_ptr(stream))
     _check(rc, "qcode_histogram")
     return hist
+
+
+def value_range(x: torch.Tensor, workspace: Workspace | None = None, stream=None) -> torch.Tensor:
+    """{vmin, vmax} over the finite values of x, as a 2-float CUDA tensor (no sync)."""
+    _check_field(x)
+    dims = tuple(int(d) for d in x.shape)
+    wsb = interp_workspace_bytes(dims, Config().to_c())
+    ws = (workspace or _default_ws.setdefault(x.device, Workspace())).get(wsb, x.device)
+    out = torch.empty(2, dtype=torch.float32, device=x.device)
+    _check(interp_value_range(_ptr(x), dims, _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream)),
+           "interp_value_range")
+    return out
 
 
 def autotune(x: torch.Tensor, radius: int = 512, stream=None):

@@ -81,25 +81,37 @@ struct LevelQ {
     float e, twoe, inv2e;
 };
 
+// Rounding by the float adder: for |v| < 2^22, v + 1.5*2^23 lies in
+// (2^23, 2^24), where floats are spaced by 1, so the sum rounds v to an
+// integer with ties to even (1.5*2^23 is even): (v + kMagic) - kMagic is
+// exactly rintf(v), and the bits of v + kMagic are kMagicBits + rintf(v).
+// For |v| >= 2^22 the result has magnitude >= 2^22 > R, so the point is an
+// outlier exactly when it is one with rintf; NaN and Inf propagate.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;
+
 // Quantize x against prediction p (Sec. III-A): q = rint((x - p) / 2e);
 // kept iff |q| < R and the reconstruction p + q*2e is within e of x.
 // Returns the code (q + R, or 0 for an outlier) and writes x' to xr.
-__device__ __forceinline__ uint32_t quantize(float x, float p, const LevelQ &L, int R, float Rf, float &xr)
+// cbias = kMagicBits - R.
+__device__ __forceinline__ uint32_t quantize(float x, float p, const LevelQ &L, uint32_t cbias, float Rf, float &xr)
 {
-    float d = x - p;
-    float v = d * L.inv2e;
-    float q = rintf(v);
+    const float d = x - p;
+    const float v = d * L.inv2e;
+    const float y = v + kMagic;
+    const float q = y - kMagic;
     bool ok = fabsf(q) < Rf;
-    int qi = ok ? (int)q : 0;
-    float r = p + (float)qi * L.twoe;
+    const float r = p + q * L.twoe;
     ok = ok && (fabsf(x - r) <= L.e);
     xr = ok ? r : x;
-    return ok ? (uint32_t)(qi + R) : 0u;
+    return ok ? __float_as_uint(y) - cbias : 0u;
 }
 
-__device__ __forceinline__ float dequantize(uint32_t code, float p, const LevelQ &L, int R, float outlier_value)
+// (code - R) as a float, exactly (|code - R| < 2^22): the float whose bits are
+// kMagicBits + (code - R) is kMagic + (code - R).
+__device__ __forceinline__ float code_to_q(uint32_t code, uint32_t cbias)
 {
-    return code ? p + (float)((int)code - R) * L.twoe : outlier_value;
+    return __uint_as_float(code + cbias) - kMagic;
 }
 
 }  // namespace gi

@@ -82,6 +82,10 @@ constexpr size_t kDecompressSmem = D_BAR + 16;
 // with 16-row columns, 4 compression CTAs fit an SM: dynamic + static (~128 B) + 1 KB reserved each
 static_assert(OY != 16 || 4 * (kCompressSmem + 128 + 1024) <= 228 * 1024, "four compression CTAs per SM");
 
+// Nonzero iff one of the two 16-bit halves of w is zero (a borrow can only set
+// bits above a zero half, never create one).
+__device__ __forceinline__ uint32_t has_zero_half(uint32_t w) { return (w - 0x00010001u) & ~w & 0x80008000u; }
+
 // ------------------------------------------------------------ cp.async (fallback path)
 __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
 {
@@ -116,6 +120,7 @@ struct Levels {
     int rank[3];  // position of each axis in the order
     int R;
     float Rf;
+    uint32_t cbias;  // kMagicBits - R
 };
 
 __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
@@ -131,6 +136,7 @@ __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
     for (int k = 0; k < 3; ++k) lv.rank[lv.order[k]] = k;
     lv.R = h->cfg.radius;
     lv.Rf = (float)lv.R;
+    lv.cbias = kMagicBits - (uint32_t)lv.R;
 }
 
 // Slab c of an item covers planes [8c, 8c+8].  It writes the outputs of
@@ -190,8 +196,8 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
     const LevelQ Lq = lv.L[l];
     const bool spline = lv.spline[l] != 0;
     const Cubic cub = lv.cub[D];
-    const int R = lv.R;
     const float Rf = lv.Rf;
+    const uint32_t cbias = lv.cbias;
 
     for (int w = threadIdx.x; w < nseg; w += NT) {
         // consecutive threads walk U first, then V, then the chunk along D
@@ -211,13 +217,13 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
             if (COMPRESS) {
                 const float x = line[o * BD];
                 float xr;
-                const uint32_t code = quantize(x, p, Lq, R, Rf, xr);
+                const uint32_t code = quantize(x, p, Lq, cbias, Rf, xr);
                 line[o * BD] = xr;
                 if (owned) sk.stage[sbase + o * SD] = (uint16_t)code;
             } else {
                 // outliers (code 0) already hold their stored value in the box
                 const uint32_t code = sk.cbox[cbase + o * KD];
-                const float xq = p + (float)((int)code - R) * Lq.twoe;
+                const float xq = p + code_to_q(code, cbias) * Lq.twoe;
                 line[o * BD] = code ? xq : line[o * BD];
             }
         };
@@ -590,12 +596,10 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
             }
             // outlier bits and histogram, one predicated atomic per code: the central
             // code R (the most frequent one) goes to this lane's private counter
-            uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
                 const bool valid = j < nvalid;
-                zmask |= (uint32_t)(valid && c == 0u) << j;
                 if (cw.smem_hist) {
                     uint32_t *bin = c == (uint32_t)cw.R ? lane_ctr : hist_s + c;
                     if (valid && c < (uint32_t)cw.bins) atomicAdd(bin, 1u);
@@ -603,6 +607,15 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
                     if (c == (uint32_t)cw.R) ++central;
                     else atomicAdd(&F.a.hist[c], 1u);
                 }
+            }
+            // outlier bits (code 0), exact per code only when a word holds a zero half
+            // or the lane's codes are cut by the field's edge
+            uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
+            if ((has_zero_half(w[0]) | has_zero_half(w[1]) | has_zero_half(w[2]) | has_zero_half(w[3])) ||
+                nvalid < 8) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    zmask |= (uint32_t)(j < nvalid && ((w[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) << j;
             }
             // the 4 lanes of a row assemble its 32-bit outlier word
             uint32_t word = zmask << (8 * sub);

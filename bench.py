@@ -145,6 +145,17 @@ def ncu_traffic(kernel: str):
 
 
 # ------------------------------------------------------------------ our arm
+def quality_summary(G, cf, x, xrec) -> dict:
+    """Untimed: the codes' entropy (bits per point, the rate an entropy coder
+    approaches), nonzero quant-codes (Fig. 4's count) and the reconstruction PSNR."""
+    q = G.quality(cf, x, xrec)
+    return {"entropy_bits_per_point": round(q["entropy_bits"], 4),
+            "code_stream_ratio_estimate": round(32.0 / q["entropy_bits"], 2) if q["entropy_bits"] > 0 else None,
+            "nonzero_code_fraction": round(q["n_nonzero"] / max(q["n"], 1), 5),
+            "max_abs_q": q["max_abs_q"], "psnr_db": round(q["psnr_db"], 3),
+            "max_abs_err": q["max_abs_err"]}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -266,6 +277,7 @@ def run_ours(args, rank, world, local):
         "roofline_step": {"bound": "hbm", "achieved": round(step_gbs, 1), "peak": peak, "unit": "GB/s",
                           "frac": round(step_gbs / peak, 4), "algorithmic_bytes_per_step": step_alg},
         "max_abs_err_over_eb": err / h.eb_abs,
+        "quality": quality_summary(G, cf, x, xrec),
         "gpu_launches": (G.launches_compress(cfg) + G.LAUNCHES_DECOMPRESS) * args.steps,
         "clocks": clocks,
     }

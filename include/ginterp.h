@@ -194,6 +194,38 @@ int interp_value_range(const float *d_x, const int64_t dims[3], float *d_range, 
 int interp_autotune(const float *d_x, const int64_t dims[3], interp_config *h_cfg,
                     double *h_profile, void *d_ws, size_t ws_bytes, interp_stream_t stream);
 
+/* Quality report of a compression (Sec. IV-D: Fig. 4 counts nonzero quant-codes; the
+ * PSNR comparison after it).  From the code histogram (2R bins, as written by
+ * interp_compress or qcode_histogram): the point count, outliers, nonzero quant-codes,
+ * the largest |q| among kept points and the Shannon entropy of the codes in bits per
+ * point (the rate an entropy coder approaches: 32 / entropy_bits estimates the ratio of
+ * the code stream).  From the field and its reconstruction (optional, both or neither):
+ * the sum and maximum of the error over finite points, the finite value range and the
+ * PSNR.  Not part of the compression path. */
+typedef struct {
+    uint64_t n;           /* points in the histogram */
+    uint64_t n_outliers;  /* code 0 */
+    uint64_t n_nonzero;   /* points whose quant-code is not 0 (code != R), outliers included */
+    uint64_t n_finite;    /* finite points of x in the error statistics (0 without x) */
+    int32_t max_abs_q;    /* largest |code - R| among kept points (code != 0) */
+    int32_t reserved;
+    double entropy_bits;  /* -sum_c p_c log2 p_c, p_c = hist[c] / n */
+    double sse;           /* sum of (x - x')^2 over finite x, in double (NaN without x) */
+    double max_abs_err;   /* max |x - x'| over finite x */
+    double vmin, vmax;    /* finite value range of x */
+    double psnr_db;       /* 20 log10(vmax - vmin) - 10 log10(sse / n_finite); +Inf if sse = 0 */
+} interp_quality;
+
+/* Scratch interp_quality_report needs (bytes). */
+size_t interp_quality_workspace_bytes(void);
+
+/* Fill *d_out (device) from d_hist (2R uint32) and, when both are non-NULL, from
+ * d_x and d_xrec (N floats each).  Stream-ordered; d_ws holds at least
+ * interp_quality_workspace_bytes() bytes.  The error sums are accumulated in double
+ * in a fixed order for a given device, so they match a float64 sum to rounding. */
+int interp_quality_report(const uint32_t *d_hist, int32_t radius, const float *d_x, const float *d_xrec,
+                          uint64_t n, interp_quality *d_out, void *d_ws, size_t ws_bytes, interp_stream_t stream);
+
 /* Measurement support (not part of the compression method): while enabled,
  * every interp_compress / interp_decompress call records a pair of CUDA events
  * on its stream immediately around its tile kernel (at most 512 pairs per kernel;

@@ -235,3 +235,46 @@ def autotune_decide(prof: np.ndarray, radius: int = 512) -> Config:
 
 def autotune(x: np.ndarray, radius: int = 512) -> Config:
     return autotune_decide(profile(x), radius)
+
+
+def quality(hist: np.ndarray, radius: int, x: np.ndarray | None = None, xrec: np.ndarray | None = None) -> dict:
+    """Quality report written from its definitions (Sec. IV-D: Fig. 4 counts the
+    nonzero quant-codes; the PSNR comparison after it), in float64:
+
+    - n = sum of the histogram, n_outliers = hist[0], n_nonzero = n - hist[R]
+      (points whose quant-code q is not 0, outliers included),
+      max_abs_q = max |c - R| over occupied bins c != 0;
+    - entropy_bits = -sum_c p_c log2 p_c with p_c = hist[c] / n (Shannon);
+    - over the finite points of x: sse = sum (x - x')^2, max_abs_err = max |x - x'|,
+      vmin / vmax, psnr_db = 20 log10(vmax - vmin) - 10 log10(sse / n_finite).
+    """
+    h = np.asarray(hist, dtype=np.float64).reshape(-1)
+    R = int(radius)
+    n = float(h.sum())
+    occ = np.nonzero(h)[0]
+    kept = occ[(occ != 0) & (occ != R)]
+    p = h[occ] / n if n else np.zeros(0)
+    out = {
+        "n": int(n), "n_outliers": int(h[0]), "n_nonzero": int(n - h[R]),
+        "max_abs_q": int(np.abs(kept - R).max()) if kept.size else 0,
+        "entropy_bits": float(-(p * np.log2(p)).sum()) if p.size else 0.0,
+    }
+    if x is None:
+        out.update(n_finite=0, sse=float("nan"), max_abs_err=float("nan"), vmin=float("nan"), vmax=float("nan"),
+                   psnr_db=float("nan"))
+        return out
+    a = np.asarray(x, dtype=np.float64).reshape(-1)
+    b = np.asarray(xrec, dtype=np.float64).reshape(-1)
+    fin = np.isfinite(a)
+    a, b = a[fin], b[fin]
+    d = a - b
+    sse = float((d * d).sum())
+    nf = int(a.size)
+    vmin, vmax = (float(a.min()), float(a.max())) if nf else (float("nan"), float("nan"))
+    if nf and sse > 0:
+        psnr = 20.0 * np.log10(vmax - vmin) - 10.0 * np.log10(sse / nf)
+    else:
+        psnr = float("inf") if nf else float("nan")
+    out.update(n_finite=nf, sse=sse, max_abs_err=float(np.abs(d).max()) if nf else float("nan"), vmin=vmin,
+               vmax=vmax, psnr_db=float(psnr))
+    return out

@@ -259,6 +259,18 @@ int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_
     return cuda_status(e);
 }
 
+size_t interp_quality_workspace_bytes(void) { return gi::quality_workspace_bytes(); }
+
+int interp_quality_report(const uint32_t *d_hist, int32_t radius, const float *d_x, const float *d_xrec, uint64_t n,
+                          interp_quality *d_out, void *d_ws, size_t ws_bytes, interp_stream_t stream)
+{
+    if (radius < 2 || radius > 32768 || !d_hist || !d_out) return INTERP_EINVAL;
+    if ((d_x == nullptr) != (d_xrec == nullptr)) return INTERP_EINVAL;
+    if (d_x && (!d_ws || ws_bytes < gi::quality_workspace_bytes())) return INTERP_EWORKSPACE;
+    return cuda_status(gi::launch_quality(d_hist, radius, d_x, d_xrec, n, d_out, d_ws,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
 double interp_alpha(double eps) { return alpha_of_eps(eps); }
 
 int interp_value_range(const float *d_x, const int64_t dims[3], float *d_range, void *d_ws, size_t ws_bytes,

@@ -161,6 +161,10 @@ cudaError_t launch_outlier_scatter(const interp_header *hdr, const uint32_t *idx
                                    uint64_t capacity, float *xrec, cudaStream_t s);
 cudaError_t launch_histogram(const uint16_t *codes, uint64_t n, int radius, uint32_t *hist, cudaStream_t s);
 
+cudaError_t launch_quality(const uint32_t *hist, int radius, const float *x, const float *xr, uint64_t n,
+                           interp_quality *out, void *ws, cudaStream_t s);
+size_t quality_workspace_bytes();
+
 int range_blocks();
 int sm_count();
 

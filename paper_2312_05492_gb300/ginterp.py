@@ -25,7 +25,8 @@ STATUS_CAPACITY, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4
 FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress", "interp_decompress",
              "qcode_histogram", "interp_autotune", "interp_timing_enable", "interp_timing_read",
              "interp_compress_noalloc", "interp_noalloc_scratch_bytes", "interp_compress_batched",
-             "interp_decompress_batched", "interp_status_string", "interp_alpha", "interp_value_range")
+             "interp_decompress_batched", "interp_status_string", "interp_alpha", "interp_value_range",
+             "interp_quality_workspace_bytes", "interp_quality_report")
 
 # kernels each call launches (memsets excluded): compress = [profile] + range or
 # header + tiles + outlier scan + outlier write; decompress = scatter + tiles
@@ -48,6 +49,13 @@ class interp_header(ctypes.Structure):
                 ("twoe", ctypes.c_float * 3), ("inv2e", ctypes.c_float * 3), ("vmin", ctypes.c_float),
                 ("vmax", ctypes.c_float), ("n_outliers", ctypes.c_uint64), ("n_nonfinite", ctypes.c_uint64),
                 ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("profile", ctypes.c_double * 18)]
+
+
+class interp_quality(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("n_outliers", ctypes.c_uint64), ("n_nonzero", ctypes.c_uint64),
+                ("n_finite", ctypes.c_uint64), ("max_abs_q", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("entropy_bits", ctypes.c_double), ("sse", ctypes.c_double), ("max_abs_err", ctypes.c_double),
+                ("vmin", ctypes.c_double), ("vmax", ctypes.c_double), ("psnr_db", ctypes.c_double)]
 
 
 class interp_compress_item(ctypes.Structure):
@@ -94,6 +102,10 @@ def load() -> ctypes.CDLL:
     lib.interp_decompress.argtypes = [dims_t, P, P, P, P, P, u64, P, P]
     lib.qcode_histogram.restype = ctypes.c_int
     lib.qcode_histogram.argtypes = [P, u64, i32, P, P]
+    lib.interp_quality_workspace_bytes.restype = ctypes.c_size_t
+    lib.interp_quality_workspace_bytes.argtypes = []
+    lib.interp_quality_report.restype = ctypes.c_int
+    lib.interp_quality_report.argtypes = [P, i32, P, P, u64, P, P, ctypes.c_size_t, P]
     lib.interp_alpha.restype = ctypes.c_double
     lib.interp_alpha.argtypes = [ctypes.c_double]
     lib.interp_value_range.restype = ctypes.c_int
@@ -156,6 +168,14 @@ def interp_decompress(dims, d_hdr, d_anchors, d_codes, d_out_idx, d_out_val, out
 
 def qcode_histogram(d_codes, n, radius, d_hist, stream) -> int:
     return load().qcode_histogram(d_codes, int(n), int(radius), d_hist, stream)
+
+
+def interp_quality_workspace_bytes() -> int:
+    return int(load().interp_quality_workspace_bytes())
+
+
+def interp_quality_report(d_hist, radius, d_x, d_xrec, n, d_out, d_ws, ws_bytes, stream) -> int:
+    return load().interp_quality_report(d_hist, int(radius), d_x, d_xrec, int(n), d_out, d_ws, int(ws_bytes), stream)
 
 
 def interp_alpha(eps: float) -> float:
@@ -386,6 +406,26 @@ def value_range(x: torch.Tensor, workspace: Workspace | None = None, stream=None
     _check(interp_value_range(_ptr(x), dims, _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream)),
            "interp_value_range")
     return out
+
+
+def quality(cf: "CompressedField", x: torch.Tensor | None = None, xrec: torch.Tensor | None = None,
+            stream=None) -> dict:
+    """Quality report of a compressed field (histogram entropy and code counts; with x
+    and xrec also the error statistics and PSNR).  Synchronises the stream."""
+    if cf.hist is None:
+        raise InterpError("the field was compressed without a histogram")
+    dev = cf.codes.device
+    out = torch.zeros(ctypes.sizeof(interp_quality), dtype=torch.uint8, device=dev)
+    ws = torch.empty(interp_quality_workspace_bytes(), dtype=torch.uint8, device=dev)
+    if (x is None) != (xrec is None):
+        raise InterpError("give both x and xrec, or neither")
+    n = int(x.numel()) if x is not None else 0
+    rc = interp_quality_report(_ptr(cf.hist), cf.cfg.radius, _ptr(x), _ptr(xrec), n, _ptr(out), _ptr(ws),
+                               ws.numel(), _stream_ptr(stream))
+    _check(rc, "interp_quality_report")
+    host = out.cpu().numpy().tobytes()
+    q = interp_quality.from_buffer_copy(host)
+    return {name: getattr(q, name) for name, _ in interp_quality._fields_ if name != "reserved"}
 
 
 def autotune(x: torch.Tensor, radius: int = 512, stream=None):

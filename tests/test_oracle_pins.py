@@ -406,3 +406,39 @@ def test_quantization_concentrates_codes_on_smooth_field():
     x3 = fields.grf((64, 64, 64), 3.0, 0).numpy()
     eb_abs, e, twoe, inv2e = O.bounds_for(x3, 1e-3, "rel")
     assert O.compress(x3, cfg, e, twoe, inv2e, eb_abs).n_outliers <= 1e-4 * x3.size
+
+
+# ---- quality report (Sec. IV-D: nonzero quant-codes of Fig. 4, entropy, PSNR)
+def test_quality_entropy_closed_forms():
+    R = 8
+    h = np.zeros(2 * R, np.uint32)
+    h[R] = 100
+    q = O.quality(h, R)
+    assert q["entropy_bits"] == 0.0 and q["n_nonzero"] == 0 and q["max_abs_q"] == 0
+    h[:] = 0
+    h[[3, 5, 9, 12]] = 7  # four equally likely codes: exactly 2 bits
+    assert abs(O.quality(h, R)["entropy_bits"] - 2.0) < 1e-15
+    h[:] = 0
+    h[R], h[R - 1], h[R + 3] = 2, 1, 1  # p = 1/2, 1/4, 1/4: 1.5 bits
+    q = O.quality(h, R)
+    assert abs(q["entropy_bits"] - 1.5) < 1e-15
+    assert q["n_nonzero"] == 2 and q["max_abs_q"] == 3 and q["n"] == 4
+    h[0] = 4  # outliers count as nonzero codes but not for max |q|
+    q = O.quality(h, R)
+    assert q["n_outliers"] == 4 and q["n_nonzero"] == 6 and q["max_abs_q"] == 3
+
+
+def test_quality_error_closed_forms():
+    rng = np.random.default_rng(3)
+    x = (rng.integers(-4096, 4096, 5000) / 1024.0).astype(np.float32)  # dyadic: x + c is exact
+    c = 2.0 ** -6
+    xr = (x + np.float32(c)).astype(np.float32)
+    x[17] = np.nan  # non-finite points are left out of the error statistics
+    x[99] = np.inf
+    q = O.quality(np.ones(4, np.uint32), 2, x, xr)
+    fin = np.isfinite(x)
+    rng_ = float(x[fin].max()) - float(x[fin].min())
+    assert q["n_finite"] == 4998
+    assert q["sse"] == 4998 * c * c and q["max_abs_err"] == c
+    assert abs(q["psnr_db"] - 20.0 * np.log10(rng_ / c)) < 1e-9
+    assert O.quality(np.ones(4, np.uint32), 2, x, np.where(fin, x, 0).astype(np.float32))["psnr_db"] == float("inf")

@@ -121,6 +121,7 @@ struct Levels {
     int R;
     float Rf;
     uint32_t cbias;  // kMagicBits - R
+    int nseg[2][3][3];  // segments of pass k of level l, [plane 0 carried][l][k]
 };
 
 __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
@@ -137,6 +138,17 @@ __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
     lv.R = h->cfg.radius;
     lv.Rf = (float)lv.R;
     lv.cbias = kMagicBits - (uint32_t)lv.R;
+    // segment counts of every pass (the same rule as run_pass), so that threads
+    // without work in a pass leave it at once
+    for (int carried = 0; carried < 2; ++carried)
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k) {
+                const int D = lv.order[k], S = 1 << l;
+                const int U = axis_u(D), V = axis_v(D);
+                const int nU = count_on(ext_of(U), lv.rank[U] < k ? S : 2 * S);
+                const int nV = count_on(ext_of(V), lv.rank[V] < k ? S : 2 * S) - ((V == 0 && carried) ? 1 : 0);
+                lv.nseg[carried][l][k] = nU * nV * chunks_of(D);
+            }
 }
 
 // Slab c of an item covers planes [8c, 8c+8].  It writes the outputs of
@@ -176,6 +188,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
     constexpr int SD = sstride(D), SU = sstride(U), SV = sstride(V);
     constexpr int KD = cstride(D), KU = cstride(U), KV = cstride(V);
     constexpr int l = S == 1 ? 0 : (S == 2 ? 1 : 2);
+    if ((int)threadIdx.x >= lv.nseg[sl.carried ? 1 : 0][l][k]) return;  // no segment for this thread
 
     // axes before D in the order sit on the s-grid, axes after it on the 2s-grid
     const bool ue = lv.rank[U] < k, ve = lv.rank[V] < k;
@@ -487,7 +500,7 @@ __device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uin
 
 // MULTI = false: a single field (index 0 everywhere, resolved at compile time).
 template <bool MULTI>
-__global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch B)
+__global__ void __launch_bounds__(NT, 4) k_compress(const __grid_constant__ CBatch B)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Levels lv;
@@ -569,7 +582,54 @@ __global__ void __launch_bounds__(NT) k_compress(const __grid_constant__ CBatch 
         const int hi = min(sl.own_hi, nzp - 1);
         const int rows = (hi - sl.own_lo + 1) * OY;
         const int sub = lane & 3;
-        for (int base = warp * 8; base < rows; base += NWARP * 8) {
+        // Fast path: every owned row of the slab lies inside the field, code rows are
+        // 16-byte aligned and the histogram bins fit in shared memory.
+        const bool fast = cw.vec_codes && cw.smem_hist && sl.g0[1] + OY <= f.n[1] && sl.g0[2] + OX <= f.n[2];
+        if (fast) {
+            const size_t plane = (size_t)f.n[1] * f.n[2];
+            uint16_t *cb = F.a.codes + ((size_t)(sl.g0[0] + sl.own_lo) * f.n[1] + sl.g0[1]) * f.n[2] + sl.g0[2] +
+                           8 * sub;
+            uint32_t *wb = F.a.bitmap + ((size_t)sl.col * f.n[0] + sl.g0[0] + sl.own_lo) * OY;
+            const uint16_t *sb = stage + sl.own_lo * STAGE_PLANE + 8 * sub;
+            const uint32_t Ru = (uint32_t)cw.R;
+            for (int row = threadIdx.x >> 2; row < rows; row += NT / 4) {
+                const int pzr = row / OY, y = row % OY;
+                const uint32_t *srow = reinterpret_cast<const uint32_t *>(sb + pzr * STAGE_PLANE + y * CP);
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[j] = srow[j];
+                const int pz = sl.own_lo + pzr;
+                if (((pz | y) & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
+                    w[0] = (w[0] & 0xffff0000u) | Ru;
+                    const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gx = sl.g0[2] + 8 * sub;
+                    F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] =
+                        box[pz * PLANE + y * EX + 8 * sub];
+                }
+                *reinterpret_cast<uint4 *>(cb + pzr * plane + (size_t)y * f.n[2]) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {  // every staged code here is < 2R
+                    const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                    atomicAdd(c == Ru ? lane_ctr : hist_s + c, 1u);
+                }
+                uint32_t zmask = 0;
+                if (has_zero_half(w[0]) | has_zero_half(w[1]) | has_zero_half(w[2]) | has_zero_half(w[3])) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        zmask |= (uint32_t)(((w[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) << j;
+                }
+                uint32_t word = zmask << (8 * sub);
+                word |= __shfl_xor_sync(0xffffffffu, word, 1);
+                word |= __shfl_xor_sync(0xffffffffu, word, 2);
+                if (sub == 0) {
+                    wb[row] = word;
+                    if (word) {
+                        const int64_t gw = ((int64_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * cw.WX + sl.g0[2] / 32;
+                        atomicAdd(&F.a.blockcnt[gw / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
+                    }
+                }
+            }
+        }
+        for (int base = warp * 8; !fast && base < rows; base += NWARP * 8) {
             const int row = base + (lane >> 2);
             const int pz = sl.own_lo + row / OY, y = row % OY;
             const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y;

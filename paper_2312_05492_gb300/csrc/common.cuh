@@ -22,7 +22,7 @@ namespace gi {
 // A CTA marches along z through a column of 2 x 4 chunks of 8^3 points
 // (16 y x 32 x owned points), one slab of 8 planes at a time.
 #ifndef GI_TILE_THREADS
-#define GI_TILE_THREADS 256
+#define GI_TILE_THREADS 192
 #endif
 #ifndef GI_TILE_ROWS
 #define GI_TILE_ROWS 16

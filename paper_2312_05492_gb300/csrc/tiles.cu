@@ -237,7 +237,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
                 // outliers (code 0) already hold their stored value in the box
                 const uint32_t code = sk.cbox[cbase + o * KD];
                 const float xq = p + code_to_q(code, cbias) * Lq.twoe;
-                line[o * BD] = code ? xq : line[o * BD];
+                if (code) line[o * BD] = xq;
             }
         };
 

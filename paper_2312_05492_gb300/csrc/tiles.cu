@@ -43,7 +43,9 @@ constexpr int CBOX_PLANE = EY * CP;              // decompression code box: all 
 constexpr int CBOX = EZ * CBOX_PLANE;
 // TMA landing buffers: dense boxes whose rows are a multiple of 16 bytes
 constexpr int XP = 36;                           // floats per landed row (x 0..35)
-constexpr int XLAND = EZ * EY * XP;
+constexpr int XPL = 8;                           // landed input planes: 1..8 of a slab (plane 0 is
+                                                 // carried, or loaded directly at a run's start)
+constexpr int XLAND = XPL * EY * XP;
 constexpr int KP = 40;                           // codes per landed row (x 0..39)
 constexpr int KLAND = EZ * EY * KP;
 constexpr uint32_t kTmaPolls = 1u << 22;         // bounded wait for one TMA box
@@ -68,19 +70,23 @@ __device__ __forceinline__ int fdiv(int w, uint32_t m) { return m ? (int)__umulh
 // dynamic shared-memory layouts: the TMA landing buffer first (the dynamic
 // shared-memory base is 128-byte aligned), then 16-byte aligned sub-arrays
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) / 16 * 16; }
+// compression: the staged codes reuse the landing buffer (the next slab's load is
+// issued once they are written out)
 constexpr size_t C_LAND = 0;
+constexpr size_t C_STAGE = C_LAND;
 constexpr size_t C_BOX = al16(C_LAND + sizeof(float) * XLAND);
-constexpr size_t C_STAGE = al16(C_BOX + sizeof(float) * BOXF);
-constexpr size_t C_HIST = al16(C_STAGE + sizeof(uint16_t) * STAGE);
+constexpr size_t C_HIST = al16(C_BOX + sizeof(float) * BOXF);
 constexpr size_t C_BAR = al16(C_HIST + sizeof(uint32_t) * HIST_SMEM_BINS);
 constexpr size_t kCompressSmem = C_BAR + 16;
+static_assert(sizeof(uint16_t) * STAGE <= sizeof(float) * XLAND, "staged codes fit the landing buffer");
 constexpr size_t D_LAND = 0;
 constexpr size_t D_BOX = al16(D_LAND + sizeof(uint16_t) * KLAND);
 constexpr size_t D_CBOX = al16(D_BOX + sizeof(float) * BOXF);
 constexpr size_t D_BAR = al16(D_CBOX + sizeof(uint16_t) * CBOX);
 constexpr size_t kDecompressSmem = D_BAR + 16;
-// with 16-row columns, 4 compression CTAs fit an SM: dynamic + static (~128 B) + 1 KB reserved each
-static_assert(OY != 16 || 4 * (kCompressSmem + 128 + 1024) <= 228 * 1024, "four compression CTAs per SM");
+// with 16-row columns, 5 compression CTAs fit an SM: dynamic + static (< 512 B) + 1 KB reserved each
+constexpr int kCompressCtas = 5;
+static_assert(OY != 16 || kCompressCtas * (kCompressSmem + 512 + 1024) <= 228 * 1024, "compression CTAs per SM");
 
 // Nonzero iff one of the two 16-bit halves of w is zero (a borrow can only set
 // bits above a zero half, never create one).
@@ -383,26 +389,26 @@ __device__ __forceinline__ void slab_of(Slab &s, const Cursor &cu, const BatchVi
 // one TMA box (thread 0; out-of-field elements are zero-filled), or, when the
 // field's rows cannot be described by a tensor map, 4-byte cp.async copies
 // of the in-field elements by all threads.
-template <typename T, int P>
+template <typename T, int P, int NPL, int Z0>
 __device__ __forceinline__ void issue_land(T *land, const T *__restrict__ src, const CUtensorMap *map, bool use_tma,
                                            uint64_t *bar, const Field &f, const Slab &s)
 {
     if (use_tma) {
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(T) * EZ * EY * P));
-            tma_load_3d(land, map, s.g0[2], s.g0[1], s.g0[0], bar);
+            mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(T) * NPL * EY * P));
+            tma_load_3d(land, map, s.g0[2], s.g0[1], s.g0[0] + Z0, bar);
         }
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nzp = min(EZ, f.n[0] - s.g0[0]);
+    const int nzp = min(NPL, f.n[0] - s.g0[0] - Z0);
     const int nyr = min(EY, f.n[1] - s.g0[1]);
     const int nxc = min(EX, f.n[2] - s.g0[2]);
     for (int r = warp; r < nzp * EY; r += NWARP) {
         const int pz = r / EY, y = r % EY;
         if (y >= nyr) continue;
-        const T *row = src + ((size_t)(s.g0[0] + pz) * f.n[1] + s.g0[1] + y) * f.n[2] + s.g0[2];
+        const T *row = src + ((size_t)(s.g0[0] + Z0 + pz) * f.n[1] + s.g0[1] + y) * f.n[2] + s.g0[2];
         T *dst = land + r * P;
         if (sizeof(T) == 4) {
             if (lane < nxc) cp_async4(dst + lane, row + lane);
@@ -461,23 +467,15 @@ __device__ __forceinline__ CWrite cwrite_of(const CField &F)
     return w;
 }
 
-// Per-lane counters of the central code live in the spare padding word of
-// staging rows 0..31 (codes occupy 32 of each row's 34 half-words).
-__device__ __forceinline__ uint32_t *central_counter(uint16_t *stage, int lane)
-{
-    return reinterpret_cast<uint32_t *>(stage + lane * CP) + OX / 2;
-}
-
 // Add the CTA's histogram counts of one field to its global bins and clear them.
 __device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uint32_t *hist_s, uint32_t &central,
-                                           uint16_t *stage)
+                                           uint32_t *lane_ctrs)
 {
     const int lane = threadIdx.x & 31;
     __syncthreads();
     if (threadIdx.x < 32) {  // fold the per-lane central counters into the register count
-        uint32_t *ctr = central_counter(stage, lane);
-        central += *ctr;
-        *ctr = 0u;
+        central += lane_ctrs[lane];
+        lane_ctrs[lane] = 0u;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) central += __shfl_xor_sync(0xffffffffu, central, off);
@@ -500,11 +498,12 @@ __device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uin
 
 // MULTI = false: a single field (index 0 everywhere, resolved at compile time).
 template <bool MULTI>
-__global__ void __launch_bounds__(NT, 4) k_compress(const __grid_constant__ CBatch B)
+__global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_constant__ CBatch B)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Levels lv;
     __shared__ int abort_flag;
+    __shared__ uint32_t lane_ctrs[32];  // per-lane counters of the central code R (shared by the warps)
     float *land = reinterpret_cast<float *>(smem + C_LAND);
     float *box = reinterpret_cast<float *>(smem + C_BOX);
     uint16_t *stage = reinterpret_cast<uint16_t *>(smem + C_STAGE);
@@ -518,14 +517,14 @@ __global__ void __launch_bounds__(NT, 4) k_compress(const __grid_constant__ CBat
         fence_barrier_init();
     }
     for (int i = threadIdx.x; i < HIST_SMEM_BINS; i += NT) hist_s[i] = 0u;
-    if (threadIdx.x < 32) *central_counter(stage, threadIdx.x) = 0u;
+    if (threadIdx.x < 32) lane_ctrs[threadIdx.x] = 0u;
     __syncthreads();
 
     uint32_t central = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t phase = 0;
     const Sink sk{stage, nullptr};
-    uint32_t *const lane_ctr = central_counter(stage, lane);
+    uint32_t *const lane_ctr = lane_ctrs + lane;
 
     Cursor cu;
     if (!cursor_start<MULTI>(cu, bv, blockIdx.x)) return;
@@ -534,7 +533,7 @@ __global__ void __launch_bounds__(NT, 4) k_compress(const __grid_constant__ CBat
     int lv_field = -1;
     {
         const int fi = MULTI ? cu.fi : 0;
-        issue_land<float, XP>(land, B.fld[fi].a.x, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f, sl);
+        issue_land<float, XP, XPL, 1>(land, B.fld[fi].a.x, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f, sl);
     }
     for (;;) {
         const int fi = MULTI ? cu.fi : 0;
@@ -547,31 +546,30 @@ __global__ void __launch_bounds__(NT, 4) k_compress(const __grid_constant__ CBat
         if (threadIdx.x == 0 && lv_field != fi) load_levels(lv, F.a.hdr);
         lv_field = fi;
 
-        // ---- landed input -> compute box (planes 0..8, or 1..8 when carried)
-        if (!wait_land(F.use_tma, bar, phase)) abort_flag = 1;
-        if (!F.use_tma) __syncthreads();  // cp.async copies of all threads visible
-        {
-            const int pz0 = sl.carried ? 1 : 0;
-            const int nitem = (EZ - pz0) * EY * 9;  // 9 groups of 4 floats per row (x 0..35)
-            for (int i = threadIdx.x; i < nitem; i += NT) {
-                const int row = pz0 * EY + i / 9, q = i % 9;
-                const float4 v = *reinterpret_cast<const float4 *>(land + row * XP + 4 * q);
-                float *d = box + row * EX + 4 * q;
-                d[0] = v.x;
-                if (q < 8) {
-                    d[1] = v.y;
-                    d[2] = v.z;
-                    d[3] = v.w;
-                }
+        // ---- input: plane 0 carried, or loaded directly at a run's start; planes 1..8 landed
+        if (!sl.carried) {
+            const int nyr = min(EY, f.n[1] - sl.g0[1]), nxc = min(EX, f.n[2] - sl.g0[2]);
+            const float *src = F.a.x + ((size_t)sl.g0[0] * f.n[1] + sl.g0[1]) * f.n[2] + sl.g0[2];
+            for (int i = threadIdx.x; i < EY * EX; i += NT) {
+                const int y = i / EX, xx = i - y * EX;
+                if (y < nyr && xx < nxc) box[i] = __ldg(src + (size_t)y * f.n[2] + xx);
             }
         }
-        __syncthreads();  // box and levels ready, landing buffer free
-        if (abort_flag) break;
-        if (has_next) {
-            const int nfi = MULTI ? nx.fi : 0;
-            const CField &N = B.fld[nfi];
-            issue_land<float, XP>(land, N.a.x, &B.map[nfi], N.use_tma, bar, N.f, sn);
+        if (!wait_land(F.use_tma, bar, phase)) abort_flag = 1;
+        if (!F.use_tma) __syncthreads();  // cp.async copies of all threads visible
+        for (int i = threadIdx.x; i < XPL * EY * 9; i += NT) {  // 9 groups of 4 floats per row (x 0..35)
+            const int row = i / 9, q = i - 9 * row;
+            const float4 v = *reinterpret_cast<const float4 *>(land + row * XP + 4 * q);
+            float *d = box + (row + EY) * EX + 4 * q;  // landed row r is box row r + EY (plane + 1)
+            d[0] = v.x;
+            if (q < 8) {
+                d[1] = v.y;
+                d[2] = v.z;
+                d[3] = v.w;
+            }
         }
+        __syncthreads();  // box and levels ready; the landing buffer now stages codes
+        if (abort_flag) break;
 
         run_slab<true>(box, sk, sl, f, lv);  // ends with a barrier
 
@@ -690,13 +688,18 @@ __global__ void __launch_bounds__(NT, 4) k_compress(const __grid_constant__ CBat
                 }
             }
         }
-        // ---- carry plane 8 into plane 0 of the next slab of the same run
-        if (has_next && nx.item == cu.item) {
-            __syncthreads();  // write-out finished reading plane 8 anchors
-            for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
+        // ---- next slab's input into the landing buffer (staged codes written out),
+        // and plane 8 carried into plane 0 when the next slab continues this run
+        __syncthreads();
+        if (has_next) {
+            const int nfi = MULTI ? nx.fi : 0;
+            const CField &N = B.fld[nfi];
+            issue_land<float, XP, XPL, 1>(land, N.a.x, &B.map[nfi], N.use_tma, bar, N.f, sn);
+            if (nx.item == cu.item)
+                for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
         }
-        __syncthreads();  // box and staging free for the next slab
-        if (!has_next || (MULTI && nx.fi != cu.fi)) flush_hist(F, cw, hist_s, central, stage);  // field done
+        __syncthreads();  // box free for the next slab
+        if (!has_next || (MULTI && nx.fi != cu.fi)) flush_hist(F, cw, hist_s, central, lane_ctrs);  // field done
         if (!has_next) break;
         cu = nx;
         sl = sn;
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(NT, 4) k_compress(const __grid_constant__ CBat
     if (abort_flag) {
         const int fi = MULTI ? cu.fi : 0;
         if (threadIdx.x == 0) atomicOr(&B.fld[fi].a.hdr->status, INTERP_STATUS_TIMEOUT);
-        flush_hist(B.fld[fi], cwrite_of(B.fld[fi]), hist_s, central, stage);
+        flush_hist(B.fld[fi], cwrite_of(B.fld[fi]), hist_s, central, lane_ctrs);
     }
     cp_async_wait_all();
 }
@@ -751,7 +754,7 @@ __global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatc
     int lv_field = -1;
     {
         const int fi = MULTI ? cu.fi : 0;
-        issue_land<uint16_t, KP>(land, B.fld[fi].a.codes, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f, sl);
+        issue_land<uint16_t, KP, EZ, 0>(land, B.fld[fi].a.codes, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f, sl);
     }
     for (;;) {
         const int fi = MULTI ? cu.fi : 0;
@@ -813,7 +816,7 @@ __global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatc
         if (has_next) {
             const int nfi = MULTI ? nx.fi : 0;
             const DField &N = B.fld[nfi];
-            issue_land<uint16_t, KP>(land, N.a.codes, &B.map[nfi], N.use_tma, bar, N.f, sn);
+            issue_land<uint16_t, KP, EZ, 0>(land, N.a.codes, &B.map[nfi], N.use_tma, bar, N.f, sn);
         }
 
         run_slab<false>(box, sk, sl, f, lv);  // ends with a barrier
@@ -950,7 +953,7 @@ cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t 
         B.fld[i].f = fs[i];
         B.fld[i].item0 = items;
         items += fs[i].items;
-        const uint32_t box[3] = {XP, EY, EZ};
+        const uint32_t box[3] = {XP, EY, XPL};  // planes 1..8 of a slab: must match issue_land<float, XP, XPL, 1>
         B.fld[i].use_tma =
             encode_tensor_map_3d(&B.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, args[i].x, args[i].dims, box) ? 1 : 0;
     }

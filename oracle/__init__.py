@@ -50,13 +50,13 @@ def _load():
     lib.orc_spline.restype = ctypes.c_float
     lib.orc_spline.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
     lib.orc_schedule_maps.restype = None
-    lib.orc_schedule_maps.argtypes = [i64, i64, i64, P, P, P, P, P]
+    lib.orc_schedule_maps.argtypes = [i64, i64, i64, P, P, P, i32, P, P]
     lib.orc_compress.restype = i64
-    lib.orc_compress.argtypes = [P, i64, i64, i64, P, P, P, i32, P, P, P, P, P, P, P, i64, P]
+    lib.orc_compress.argtypes = [P, i64, i64, i64, P, P, P, i32, i32, P, P, P, P, P, P, P, i64, P]
     lib.orc_decompress.restype = ctypes.c_int
-    lib.orc_decompress.argtypes = [i64, i64, i64, P, P, P, i32, P, P, P, P, P, i64, P]
+    lib.orc_decompress.argtypes = [i64, i64, i64, P, P, P, i32, i32, P, P, P, P, P, i64, P]
     lib.orc_predict_original.restype = None
-    lib.orc_predict_original.argtypes = [P, i64, i64, i64, P, P, P, P, P]
+    lib.orc_predict_original.argtypes = [P, i64, i64, i64, P, P, P, i32, P, P]
     lib.orc_histogram.restype = None
     lib.orc_histogram.argtypes = [P, i64, i32, P]
     lib.orc_profile.restype = None
@@ -82,11 +82,14 @@ class Config:
     order: axes (0=z, 1=y, 2=x) in processing order within every level.
     level_kind[l]: stride 2**l uses 0 = linear only, 1 = splines by neighbour count.
     cubic_kind[axis]: 0 = not-a-knot, 1 = natural.
+    domain_x: neighbour domain along x, 8 (the closed 8^3 chunk, Sec. IV-A) or 32
+      (the x-extended 32x8x8 block of Sec. IV-C).
     """
     order: tuple = (0, 1, 2)
     level_kind: tuple = (1, 1, 1)
     cubic_kind: tuple = (0, 0, 0)
     radius: int = 512
+    domain_x: int = 8
 
 
 @dataclass
@@ -145,7 +148,7 @@ def schedule_maps(dims, cfg: Config):
     pm = np.zeros(n, np.uint8)
     km = np.zeros(n, np.uint8)
     _load().orc_schedule_maps(*[int(d) for d in dims], _ptr(_i32(cfg.order)), _ptr(_i32(cfg.level_kind)),
-                              _ptr(_i32(cfg.cubic_kind)), _ptr(pm), _ptr(km))
+                              _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x), _ptr(pm), _ptr(km))
     return pm.reshape(dims), km.reshape(dims)
 
 
@@ -155,7 +158,8 @@ def predict_original(x: np.ndarray, cfg: Config):
     pred = np.zeros_like(x)
     kind = np.zeros(x.shape, np.uint8)
     _load().orc_predict_original(_ptr(x), *[int(d) for d in x.shape], _ptr(_i32(cfg.order)),
-                                 _ptr(_i32(cfg.level_kind)), _ptr(_i32(cfg.cubic_kind)), _ptr(pred), _ptr(kind))
+                                 _ptr(_i32(cfg.level_kind)), _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x),
+                                 _ptr(pred), _ptr(kind))
     return pred, kind
 
 
@@ -187,7 +191,8 @@ def compress(x: np.ndarray, cfg: Config, e, twoe, inv2e, eb_abs: float = float("
     twoe = np.ascontiguousarray(twoe, np.float32)
     inv2e = np.ascontiguousarray(inv2e, np.float32)
     cnt = _load().orc_compress(_ptr(x), *dims, _ptr(_i32(cfg.order)), _ptr(_i32(cfg.level_kind)),
-                               _ptr(_i32(cfg.cubic_kind)), int(cfg.radius), _ptr(e), _ptr(twoe), _ptr(inv2e),
+                               _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x), int(cfg.radius), _ptr(e), _ptr(twoe),
+                               _ptr(inv2e),
                                _ptr(anchors), _ptr(codes), _ptr(out_idx), _ptr(out_val), cap, _ptr(xr))
     if cnt < 0:
         raise RuntimeError(f"oracle compress failed ({cnt})")
@@ -203,7 +208,7 @@ def decompress(c: Compressed) -> np.ndarray:
     idx = np.ascontiguousarray(c.out_idx, np.uint32)
     val = np.ascontiguousarray(c.out_val, np.float32)
     rc = _load().orc_decompress(*c.dims, _ptr(_i32(c.cfg.order)), _ptr(_i32(c.cfg.level_kind)),
-                                _ptr(_i32(c.cfg.cubic_kind)), int(c.cfg.radius), _ptr(c.twoe),
+                                _ptr(_i32(c.cfg.cubic_kind)), int(c.cfg.domain_x), int(c.cfg.radius), _ptr(c.twoe),
                                 _ptr(np.ascontiguousarray(c.anchors, np.float32)), _ptr(codes), _ptr(idx), _ptr(val),
                                 int(idx.size), _ptr(xr))
     if rc != 0:
@@ -231,6 +236,7 @@ def autotune_decide(prof: np.ndarray, radius: int = 512) -> Config:
     ck = np.zeros(3, np.int32)
     _load().orc_autotune_decide(_ptr(np.ascontiguousarray(prof, np.float64)), _ptr(order), _ptr(lk), _ptr(ck))
     return Config(tuple(int(v) for v in order), tuple(int(v) for v in lk), tuple(int(v) for v in ck), radius)
+
 
 
 def autotune(x: np.ndarray, radius: int = 512) -> Config:

@@ -14,7 +14,10 @@
  *
  * Readings of the paper taken here (each is also listed in the design doc):
  *   - neighbour domain is the closed 8^3 chunk [8*floor(n/8), min(.+8, n_d-1)]
- *     along the interpolation axis (Sec. IV-A, Fig. 3);
+ *     along the interpolation axis (Sec. IV-A, Fig. 3); optionally, along x, the
+ *     closed 32-point block [32*floor(n/32), min(.+32, n_x-1)] of the GPU
+ *     design's 32x8x8 data blocks (Sec. IV-C: four 8^3 chunks share their points
+ *     along x).  Anchors stay on the stride-8 grid either way;
  *   - the axis processed later in a level covers the whole finer grid (Fig. 3);
  *   - reconstruction from the integer code: x' = p + (float)(code - R) * 2e;
  *   - natural cubic uses the float nearest 1/40 as a multiplier.
@@ -130,11 +133,12 @@ static int pass_of(const int64_t c[3], const int order[3], int *axis, int *level
 }
 
 /* Stencil kind from the neighbour-count rule (Sec. IV-B.1) within the closed
- * chunk along the interpolation axis. */
-static int stencil_kind(int64_t n, int64_t s, int64_t nd, int spline, int cubic_kind)
+ * neighbour domain of `dom` points along the interpolation axis (8: the chunk;
+ * 32: the x-extended block). */
+static int stencil_kind(int64_t n, int64_t s, int64_t nd, int spline, int cubic_kind, int64_t dom)
 {
-    int64_t lo = 8 * (n / 8);
-    int64_t hi = lo + 8;
+    int64_t lo = dom * (n / dom);
+    int64_t hi = lo + dom;
     if (hi > nd - 1) hi = nd - 1;
     int has_m3 = (n - 3 * s >= lo);
     int has_p1 = (n + s <= hi);
@@ -150,11 +154,12 @@ static int stencil_kind(int64_t n, int64_t s, int64_t nd, int spline, int cubic_
 
 /* Per-point schedule: pass id (255 for anchors) and stencil kind. */
 void orc_schedule_maps(int64_t nz, int64_t ny, int64_t nx, const int32_t order_in[3],
-                       const int32_t level_kind[3], const int32_t cubic_kind[3],
+                       const int32_t level_kind[3], const int32_t cubic_kind[3], int32_t domain_x,
                        uint8_t *pass_map, uint8_t *kind_map)
 {
     int order[3] = {order_in[0], order_in[1], order_in[2]};
     int64_t dims[3] = {nz, ny, nx};
+    int64_t dom[3] = {8, 8, domain_x == 32 ? 32 : 8};
     for (int64_t z = 0; z < nz; ++z)
         for (int64_t y = 0; y < ny; ++y)
             for (int64_t x = 0; x < nx; ++x) {
@@ -169,22 +174,24 @@ void orc_schedule_maps(int64_t nz, int64_t ny, int64_t nx, const int32_t order_i
                 }
                 pass_map[i] = (uint8_t)p;
                 kind_map[i] = (uint8_t)stencil_kind(c[axis], (int64_t)1 << level, dims[axis],
-                                                    level_kind[level], cubic_kind[axis]);
+                                                    level_kind[level], cubic_kind[axis], dom[axis]);
             }
 }
 
 /* Shared traversal state of compress / decompress / debug prediction. */
 typedef struct {
     int64_t dims[3];
+    int64_t dom[3];   /* neighbour domain along each axis: 8, or 32 along x */
     int order[3];
     int level_kind[3];
     int cubic_kind[3];
 } sched_t;
 
 static void sched_init(sched_t *S, int64_t nz, int64_t ny, int64_t nx, const int32_t order[3],
-                       const int32_t level_kind[3], const int32_t cubic_kind[3])
+                       const int32_t level_kind[3], const int32_t cubic_kind[3], int32_t domain_x)
 {
     S->dims[0] = nz; S->dims[1] = ny; S->dims[2] = nx;
+    S->dom[0] = 8; S->dom[1] = 8; S->dom[2] = domain_x == 32 ? 32 : 8;
     for (int a = 0; a < 3; ++a) {
         S->order[a] = order[a];
         S->level_kind[a] = level_kind[a];
@@ -201,7 +208,7 @@ static float predict_point(const sched_t *S, const float *v, const uint8_t *know
     int64_t s = (int64_t)1 << l;
     int64_t stride_d = (d == 2) ? 1 : (d == 1) ? S->dims[2] : S->dims[1] * S->dims[2];
     int64_t i = (c[0] * S->dims[1] + c[1]) * S->dims[2] + c[2];
-    int kind = stencil_kind(c[d], s, S->dims[d], S->level_kind[l], S->cubic_kind[d]);
+    int kind = stencil_kind(c[d], s, S->dims[d], S->level_kind[l], S->cubic_kind[d], S->dom[d]);
     float m3 = 0.0f, m1, p1 = 0.0f, p3 = 0.0f;
     int64_t im1 = i - s * stride_d, ip1 = i + s * stride_d;
     int64_t im3 = i - 3 * s * stride_d, ip3 = i + 3 * s * stride_d;
@@ -341,12 +348,12 @@ static void fill_anchors(const sched_t *S, const float *x, float *anchors, float
  * schedule; cannot happen for a correct one).  xr receives x'. */
 int64_t orc_compress(const float *x, int64_t nz, int64_t ny, int64_t nx,
                      const int32_t order[3], const int32_t level_kind[3], const int32_t cubic_kind[3],
-                     int32_t radius, const float e[3], const float twoe[3], const float inv2e[3],
+                     int32_t domain_x, int32_t radius, const float e[3], const float twoe[3], const float inv2e[3],
                      float *anchors, uint16_t *codes, uint32_t *out_idx, float *out_val,
                      int64_t capacity, float *xr)
 {
     sched_t S;
-    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind);
+    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x);
     int64_t n = nz * ny * nx;
     uint8_t *known = (uint8_t *)calloc((size_t)n, 1);
     if (!known) return -3;
@@ -393,12 +400,12 @@ static void decompress_visit(void *vctx, const int64_t c[3], int d, int l)
  * undefined read / missing outlier value. */
 int orc_decompress(int64_t nz, int64_t ny, int64_t nx,
                    const int32_t order[3], const int32_t level_kind[3], const int32_t cubic_kind[3],
-                   int32_t radius, const float twoe[3],
+                   int32_t domain_x, int32_t radius, const float twoe[3],
                    const float *anchors, const uint16_t *codes,
                    const uint32_t *out_idx, const float *out_val, int64_t n_out, float *xr)
 {
     sched_t S;
-    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind);
+    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x);
     int64_t n = nz * ny * nx;
     uint8_t *known = (uint8_t *)calloc((size_t)n, 1);
     if (!known) return -3;
@@ -439,10 +446,10 @@ static void predict_visit(void *vctx, const int64_t c[3], int d, int l)
 
 void orc_predict_original(const float *x, int64_t nz, int64_t ny, int64_t nx,
                           const int32_t order[3], const int32_t level_kind[3],
-                          const int32_t cubic_kind[3], float *pred, uint8_t *kind)
+                          const int32_t cubic_kind[3], int32_t domain_x, float *pred, uint8_t *kind)
 {
     sched_t S;
-    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind);
+    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x);
     int64_t n = nz * ny * nx;
     for (int64_t i = 0; i < n; ++i) {
         pred[i] = x[i];

@@ -270,7 +270,8 @@ def _random_cfg(rng):
     return O.Config(order=tuple(int(v) for v in rng.permutation(3)),
                     level_kind=tuple(int(v) for v in rng.integers(0, 2, 3)),
                     cubic_kind=tuple(int(v) for v in rng.integers(0, 2, 3)),
-                    radius=int(rng.choice([2, 8, 64, 512, 32768])))
+                    radius=int(rng.choice([2, 8, 64, 512, 32768])),
+                    domain_x=int(rng.choice([8, 32])))
 
 
 def _check_roundtrip(x, cfg, eb, mode, rng):
@@ -442,3 +443,70 @@ def test_quality_error_closed_forms():
     assert q["sse"] == 4998 * c * c and q["max_abs_err"] == c
     assert abs(q["psnr_db"] - 20.0 * np.log10(rng_ / c)) < 1e-9
     assert O.quality(np.ones(4, np.uint32), 2, x, np.where(fin, x, 0).astype(np.float32))["psnr_db"] == float("inf")
+
+
+# ---- x-extended neighbour domain (Sec. IV-C: 32x8x8 blocks share points along x)
+def _cubic_in_x(dims):
+    """f = (x - 19)^3 + small linear terms in y and z: integer, float32-exact."""
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=np.int64) for n in dims], indexing="ij")
+    return ((x - 19) ** 3 + 2 * y - 3 * z).astype(np.float32)
+
+
+def test_x_domain_32_makes_stride4_x_points_cubic():
+    """With the 32-point domain along x, a stride-4 point at x = 12 has neighbours
+    0, 8, 16, 24 in its block: the not-a-knot cubic reproduces a cubic in x exactly.
+    Inside the closed 8^3 chunk it only has 8 and 16 (linear): not exact."""
+    dims = (9, 9, 70)
+    f = _cubic_in_x(dims)
+    c32 = O.Config(order=(0, 1, 2), level_kind=(1, 1, 1), cubic_kind=(0, 0, 0), domain_x=32)
+    c8 = O.Config(order=(0, 1, 2), level_kind=(1, 1, 1), cubic_kind=(0, 0, 0), domain_x=8)
+    p32, k32 = O.predict_original(f, c32)
+    p8, k8 = O.predict_original(f, c8)
+    for x in (12, 20, 44, 52):  # interior stride-4 points of the blocks [0, 32] and [32, 64]
+        assert p32[0, 0, x] == f[0, 0, x] and k32[0, 0, x] == O.K_CUBIC_NAK
+        assert p8[0, 0, x] != f[0, 0, x] and k8[0, 0, x] == O.K_LINEAR
+    # the tail block [64, 69]: x = 68 has 64 (and 60 outside the block) -> a copy of x = 64
+    assert k32[0, 0, 68] == O.K_COPY and p32[0, 0, 68] == f[0, 0, 64]
+
+
+def test_x_domain_32_exactness_matches_the_stencil_kinds():
+    """On a cubic-in-x field, a point predicted along x is exact iff its stencil is
+    the not-a-knot cubic (the others do not reproduce degree 3); the extended domain
+    turns more points cubic than the closed chunk does."""
+    dims = (17, 9, 75)
+    f = _cubic_in_x(dims)
+    counts = {}
+    for dom in (8, 32):
+        cfg = O.Config(order=(0, 1, 2), level_kind=(1, 1, 1), cubic_kind=(0, 0, 0), domain_x=dom)
+        pred, kind = O.predict_original(f, cfg)
+        pm, _ = O.schedule_maps(dims, cfg)
+        along_x = (pm != 255) & (pm % 3 == 2)  # third pass of each level: the x pass
+        exact = pred == f
+        assert np.array_equal(exact[along_x], (kind == O.K_CUBIC_NAK)[along_x]), dom
+        counts[dom] = int((kind[along_x] == O.K_CUBIC_NAK).sum())
+    assert counts[32] > counts[8]
+
+
+def test_x_domain_32_equals_chunk_domain_on_narrow_fields():
+    """With nx <= 9 the 32-point block along x is the chunk itself: identical results."""
+    rng = np.random.default_rng(32)
+    for dims in [(9, 12, 9), (20, 7, 5), (3, 17, 1)]:
+        x = rng.standard_normal(dims).astype(np.float32).cumsum(axis=0)
+        for _ in range(4):
+            cfg = _random_cfg(rng)
+            eb_abs, e, twoe, inv2e = O.bounds_for(x, 1e-3, "rel")
+            a = O.compress(x, O.Config(cfg.order, cfg.level_kind, cfg.cubic_kind, cfg.radius, 8), e, twoe, inv2e)
+            b = O.compress(x, O.Config(cfg.order, cfg.level_kind, cfg.cubic_kind, cfg.radius, 32), e, twoe, inv2e)
+            assert np.array_equal(a.codes, b.codes) and np.array_equal(a.xrec.view(np.int32), b.xrec.view(np.int32))
+
+
+def test_x_domain_32_roundtrip():
+    """Round trip with the x-extended domain on shapes spanning several 32-blocks
+    and ragged tails: every neighbour read is already defined, exact replay, bounds."""
+    rng = np.random.default_rng(3232)
+    for dims in [(9, 9, 97), (17, 10, 64), (12, 17, 33), (5, 3, 130)]:
+        x = rng.standard_normal(dims).astype(np.float32).cumsum(axis=2).cumsum(axis=0)
+        for _ in range(3):
+            cfg = _random_cfg(rng)
+            cfg.domain_x = 32
+            _check_roundtrip(x, cfg, float(10 ** rng.uniform(-4, -2)), "rel", rng)

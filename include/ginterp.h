@@ -68,6 +68,10 @@ typedef struct {
                               device from a 4x4x4 sampling profile (Sec. IV-B.2) */
     int32_t radius;        /* R: codes q with |q| < R are kept, others become outliers;
                               2 <= R <= 32768 (codes are uint16, code 0 marks an outlier) */
+    int32_t domain_x;      /* neighbour domain along x: 0 or 8 = the closed 8^3 chunk
+                              (Sec. IV-A, Fig. 3); 32 = the closed 32-point block of the
+                              32x8x8 data blocks, whose four chunks share points along x
+                              (Sec. IV-C).  Anchors stay on the stride-8 grid either way. */
     double alpha;          /* error-bound reduction factor; <= 0 selects Eq. 1 A(eps) in
                               relative mode and 1 in absolute mode */
 } interp_config;

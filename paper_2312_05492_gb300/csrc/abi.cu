@@ -41,6 +41,7 @@ bool cfg_ok(const interp_config *c)
     }
     if (seen != 7) return false;
     if (c->eb_mode != 0 && c->eb_mode != 1) return false;
+    if (c->domain_x != 0 && c->domain_x != 8 && c->domain_x != 32) return false;
     if (c->autotune != 0 && c->autotune != 1) return false;
     if (c->radius < 2 || c->radius > 32768) return false;
     if (std::isnan(c->alpha) || std::isinf(c->alpha)) return false;
@@ -167,7 +168,7 @@ int interp_compress_batched(const interp_compress_item *items, int n, interp_str
                 e = gi::launch_header_init(it.d_hdr, d, it.eb, c, alpha, s);
         }
         args[i] = gi::CompressArgs{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
-                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0};
+                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0, c.domain_x == 32};
     }
     if (e == cudaSuccess) {
         timing_mark(0, 0, s);

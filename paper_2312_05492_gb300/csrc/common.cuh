@@ -131,6 +131,7 @@ struct CompressArgs {
     int radius;
     interp_header *hdr;
     bool vec_codes;  // codes 16-byte aligned and nx % 8 == 0: 8-code vector stores
+    bool xdom32;     // x-extended neighbour domain requested (cfg.domain_x == 32)
 };
 
 struct DecompressArgs {

@@ -37,6 +37,7 @@ __device__ void write_bounds(interp_header *h, Dims d, double eb, const interp_c
     h->cfg.eb_mode = cfg.eb_mode;
     h->cfg.autotune = cfg.autotune;
     h->cfg.radius = cfg.radius;
+    h->cfg.domain_x = cfg.domain_x;
     h->cfg.alpha = cfg.alpha;
     const double eb_abs = cfg.eb_mode ? eb * ((double)vmax - (double)vmin) : eb;
     h->eb = eb;

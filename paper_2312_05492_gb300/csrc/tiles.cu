@@ -127,6 +127,7 @@ struct Levels {
     int R;
     float Rf;
     uint32_t cbias;  // kMagicBits - R
+    int xdom32;      // neighbour domain along x: the column's 32-point block (else the chunk)
     int nseg[2][3][3];  // segments of pass k of level l, [plane 0 carried][l][k]
 };
 
@@ -144,6 +145,7 @@ __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
     lv.R = h->cfg.radius;
     lv.Rf = (float)lv.R;
     lv.cbias = kMagicBits - (uint32_t)lv.R;
+    lv.xdom32 = h->cfg.domain_x == 32;
     // segment counts of every pass (the same rule as run_pass), so that threads
     // without work in a pass leave it at once
     for (int carried = 0; carried < 2; ++carried)
@@ -183,7 +185,7 @@ struct Sink {
 
 // INTERIOR: the slab's whole box lies inside the field and every chunk is
 // full, so no line or chunk needs the field-edge checks.
-template <bool COMPRESS, bool INTERIOR, int S, int D>
+template <bool COMPRESS, bool INTERIOR, int S, int D, bool XDOM = false>
 __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk, const Slab &sl, const Field &f,
                                          const Levels &lv, int k)
 {
@@ -248,7 +250,32 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
         };
 
         const int hi = INTERIOR ? 8 : min(8, f.n[D] - 1 - gd);  // last offset of the (possibly truncated) chunk
-        if (hi == 8) {
+        if (D == 2 && XDOM) {
+            // x-extended domain (Sec. IV-C): neighbours anywhere in the column's
+            // 32-point block, box x in [0, hiX]; the neighbour-count rule per point
+            const int hiX = INTERIOR ? OX : min(OX, f.n[2] - 1 - sl.g0[2]);
+#pragma unroll
+            for (int o = S; o < 8; o += 2 * S) {
+                if (o > hi) break;
+                const int X = dlo + o;
+                const bool has_m3 = X - 3 * S >= 0;
+                const bool has_p1 = X + S <= hiX;
+                const bool has_p3 = X + 3 * S <= hiX;
+                const float m1 = line[(o - S) * BD];
+                float p;
+                if (!has_p1) {
+                    p = m1;
+                } else {
+                    const float p1 = line[(o + S) * BD];
+                    if (!spline) p = sp_linear(m1, p1);
+                    else if (has_m3 && has_p3) p = sp_cubic(cub, line[(o - 3 * S) * BD], m1, p1, line[(o + 3 * S) * BD]);
+                    else if (has_m3) p = sp_quad_left(line[(o - 3 * S) * BD], m1, p1);
+                    else if (has_p3) p = sp_quad_right(m1, p1, line[(o + 3 * S) * BD]);
+                    else p = sp_linear(m1, p1);
+                }
+                emit(o, p);
+            }
+        } else if (hi == 8) {
             if (S == 4) {
                 emit(4, sp_linear(line[0], line[8 * BD]));
             } else if (S == 2) {
@@ -307,7 +334,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
     }
 }
 
-template <bool COMPRESS, bool INTERIOR, int S>
+template <bool COMPRESS, bool INTERIOR, int S, bool XDOM>
 __device__ __forceinline__ void run_level(float *box, const Sink &sk, const Slab &sl, const Field &f,
                                           const Levels &lv)
 {
@@ -316,24 +343,48 @@ __device__ __forceinline__ void run_level(float *box, const Sink &sk, const Slab
         const int d = lv.order[k];
         if (d == 0) run_pass<COMPRESS, INTERIOR, S, 0>(box, sk, sl, f, lv, k);
         else if (d == 1) run_pass<COMPRESS, INTERIOR, S, 1>(box, sk, sl, f, lv, k);
-        else run_pass<COMPRESS, INTERIOR, S, 2>(box, sk, sl, f, lv, k);
+        else run_pass<COMPRESS, INTERIOR, S, 2, XDOM>(box, sk, sl, f, lv, k);
         __syncthreads();
     }
 }
 
-template <bool COMPRESS>
-__device__ __forceinline__ void run_slab(float *box, const Sink &sk, const Slab &sl, const Field &f,
-                                         const Levels &lv)
+template <bool COMPRESS, bool XDOM>
+__device__ __forceinline__ void run_levels(float *box, const Sink &sk, const Slab &sl, const Field &f,
+                                           const Levels &lv)
 {
     const bool interior = sl.g0[0] + 8 <= f.n[0] - 1 && sl.g0[1] + OY <= f.n[1] - 1 && sl.g0[2] + OX <= f.n[2] - 1;
     if (interior) {
-        run_level<COMPRESS, true, 4>(box, sk, sl, f, lv);
-        run_level<COMPRESS, true, 2>(box, sk, sl, f, lv);
-        run_level<COMPRESS, true, 1>(box, sk, sl, f, lv);
+        run_level<COMPRESS, true, 4, XDOM>(box, sk, sl, f, lv);
+        run_level<COMPRESS, true, 2, XDOM>(box, sk, sl, f, lv);
+        run_level<COMPRESS, true, 1, XDOM>(box, sk, sl, f, lv);
     } else {
-        run_level<COMPRESS, false, 4>(box, sk, sl, f, lv);
-        run_level<COMPRESS, false, 2>(box, sk, sl, f, lv);
-        run_level<COMPRESS, false, 1>(box, sk, sl, f, lv);
+        run_level<COMPRESS, false, 4, XDOM>(box, sk, sl, f, lv);
+        run_level<COMPRESS, false, 2, XDOM>(box, sk, sl, f, lv);
+        run_level<COMPRESS, false, 1, XDOM>(box, sk, sl, f, lv);
+    }
+}
+
+// The x-extended domain is an option: compression instantiates a kernel with it
+// only when a field asks for it (XDOM); decompression, whose configuration is on
+// the device, reaches it through an out-of-line call so that the default passes
+// keep their code size.
+template <bool COMPRESS>
+__device__ __noinline__ void run_levels_xdom(float *box, const Sink &sk, const Slab &sl, const Field &f,
+                                             const Levels &lv)
+{
+    run_levels<COMPRESS, true>(box, sk, sl, f, lv);
+}
+
+template <bool COMPRESS, bool XDOM>
+__device__ __forceinline__ void run_slab(float *box, const Sink &sk, const Slab &sl, const Field &f,
+                                         const Levels &lv)
+{
+    if (COMPRESS) {
+        if (XDOM && lv.xdom32) run_levels<COMPRESS, XDOM>(box, sk, sl, f, lv);
+        else run_levels<COMPRESS, false>(box, sk, sl, f, lv);
+    } else {
+        if (lv.xdom32) run_levels_xdom<COMPRESS>(box, sk, sl, f, lv);
+        else run_levels<COMPRESS, false>(box, sk, sl, f, lv);
     }
 }
 
@@ -497,7 +548,8 @@ __device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uin
 }
 
 // MULTI = false: a single field (index 0 everywhere, resolved at compile time).
-template <bool MULTI>
+// XDOM: some field of the launch uses the x-extended neighbour domain.
+template <bool MULTI, bool XDOM>
 __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_constant__ CBatch B)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -571,7 +623,7 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_con
         __syncthreads();  // box and levels ready; the landing buffer now stages codes
         if (abort_flag) break;
 
-        run_slab<true>(box, sk, sl, f, lv);  // ends with a barrier
+        run_slab<true, XDOM>(box, sk, sl, f, lv);  // ends with a barrier
 
         // ---- owned planes: codes (16-byte stores), anchors, histogram, bitmap words.
         // A warp takes 8 consecutive rows of one plane, 4 lanes x 8 codes per row.
@@ -819,7 +871,7 @@ __global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatc
             issue_land<uint16_t, KP, EZ, 0>(land, N.a.codes, &B.map[nfi], N.use_tma, bar, N.f, sn);
         }
 
-        run_slab<false>(box, sk, sl, f, lv);  // ends with a barrier
+        run_slab<false, false>(box, sk, sl, f, lv);  // ends with a barrier
 
         // ---- write the owned planes: 8 lanes x 4 values per row, 4 rows per warp
         const int nzp = min(EZ, f.n[0] - sl.g0[0]);
@@ -857,7 +909,7 @@ __global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatc
 
 // ------------------------------------------------------------ host side
 constexpr int kMaxDevices = 64;
-int compress_grid[kMaxDevices], compress_grid_multi[kMaxDevices];
+int compress_grid[4][kMaxDevices];  // [MULTI + 2 XDOM]
 int decompress_grid[kMaxDevices], decompress_grid_multi[kMaxDevices];
 
 // Opt in to the kernel's dynamic shared memory and size the persistent grid
@@ -939,8 +991,11 @@ cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t 
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     int grid = 0;
-    cudaError_t e = n > 1 ? prepare(k_compress<true>, kCompressSmem, compress_grid_multi, grid)
-                          : prepare(k_compress<false>, kCompressSmem, compress_grid, grid);
+    bool xdom = false;
+    for (int i = 0; i < n; ++i) xdom = xdom || args[i].xdom32;
+    auto kernel = n > 1 ? (xdom ? k_compress<true, true> : k_compress<true, false>)
+                        : (xdom ? k_compress<false, true> : k_compress<false, false>);
+    cudaError_t e = prepare(kernel, kCompressSmem, compress_grid[(n > 1 ? 1 : 0) + (xdom ? 2 : 0)], grid);
     if (e != cudaSuccess) return e;
     thread_local CBatch B;  // large parameter block, filled on the host
     std::memset(&B, 0, sizeof(B));
@@ -960,8 +1015,7 @@ cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t 
     B.n = n;
     B.items = items;
     if (items < grid) grid = items;
-    if (n > 1) k_compress<true><<<grid, NT, kCompressSmem, s>>>(B);
-    else k_compress<false><<<grid, NT, kCompressSmem, s>>>(B);
+    kernel<<<grid, NT, kCompressSmem, s>>>(B);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ LAUNCHES_DECOMPRESS = 2
 class interp_config(ctypes.Structure):
     _fields_ = [("dim_order", ctypes.c_int32 * 3), ("level_kind", ctypes.c_int32 * 3),
                 ("cubic_kind", ctypes.c_int32 * 3), ("eb_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("radius", ctypes.c_int32), ("alpha", ctypes.c_double)]
+                ("radius", ctypes.c_int32), ("domain_x", ctypes.c_int32), ("alpha", ctypes.c_double)]
 
 
 class interp_header(ctypes.Structure):
@@ -236,6 +236,7 @@ class Config:
 
     level_kind is indexed by level l (stride 2**l): 0 = linear only, 1 = splines.
     cubic_kind is indexed by axis (0=z, 1=y, 2=x): 0 = not-a-knot, 1 = natural.
+    domain_x: neighbour domain along x, 8 (the 8^3 chunk) or 32 (the x-extended block).
     """
     dim_order: tuple = (0, 1, 2)
     level_kind: tuple = (1, 1, 1)
@@ -244,6 +245,7 @@ class Config:
     autotune: bool = False
     radius: int = 512
     alpha: float = 0.0
+    domain_x: int = 8
 
     def to_c(self) -> interp_config:
         c = interp_config()
@@ -253,6 +255,7 @@ class Config:
         c.eb_mode = 1 if self.eb_mode == "rel" else 0
         c.autotune = 1 if self.autotune else 0
         c.radius = int(self.radius)
+        c.domain_x = int(self.domain_x)
         c.alpha = float(self.alpha)
         return c
 

@@ -25,7 +25,8 @@ def gpu_roundtrip(x_np: np.ndarray, eb: float, cfg: G.Config, capacity: int | No
 
 def oracle_cfg_from_header(h, radius: int) -> O.Config:
     return O.Config(order=tuple(h.cfg.dim_order), level_kind=tuple(h.cfg.level_kind),
-                    cubic_kind=tuple(h.cfg.cubic_kind), radius=radius)
+                    cubic_kind=tuple(h.cfg.cubic_kind), radius=radius,
+                    domain_x=32 if h.cfg.domain_x == 32 else 8)
 
 
 def assert_parity(x_np: np.ndarray, eb: float, cfg: G.Config, capacity: int | None = None, check_hist=True):
@@ -43,11 +44,13 @@ def assert_parity(x_np: np.ndarray, eb: float, cfg: G.Config, capacity: int | No
     # configuration: the oracle's own autotune decision when autotuning
     if cfg.autotune:
         ocfg = O.autotune(x_np, cfg.radius)
+        ocfg.domain_x = 32 if cfg.domain_x == 32 else 8
         prof = O.profile(x_np)
         assert np.array_equal(np.array(h.profile[:], np.float64).view(np.uint64), prof.view(np.uint64))
     else:
         ocfg = O.Config(order=tuple(cfg.dim_order), level_kind=tuple(cfg.level_kind),
-                        cubic_kind=tuple(cfg.cubic_kind), radius=cfg.radius)
+                        cubic_kind=tuple(cfg.cubic_kind), radius=cfg.radius,
+                        domain_x=32 if cfg.domain_x == 32 else 8)
     assert tuple(h.cfg.dim_order) == tuple(ocfg.order)
     assert tuple(h.cfg.level_kind) == tuple(ocfg.level_kind)
     assert tuple(h.cfg.cubic_kind) == tuple(ocfg.cubic_kind)

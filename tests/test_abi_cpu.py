@@ -44,9 +44,9 @@ def test_library_exports_every_declared_function(G):
 
 
 def test_struct_layouts(G):
-    assert ctypes.sizeof(G.interp_config) == 56
-    assert ctypes.sizeof(G.interp_header) == 320
-    assert G.interp_header.profile.offset == 176
+    assert ctypes.sizeof(G.interp_config) == 64
+    assert ctypes.sizeof(G.interp_header) == 328
+    assert G.interp_header.profile.offset == 184
 
 
 def test_anchor_count_and_workspace(G):

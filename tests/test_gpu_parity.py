@@ -56,9 +56,27 @@ def test_odd_shapes_random_configs(shape):
                        cubic_kind=tuple(int(v) for v in rng.integers(0, 2, 3)),
                        eb_mode=str(rng.choice(["rel", "abs"])),
                        radius=int(rng.choice([2, 16, 512, 4096, 32768])),
-                       alpha=float(rng.choice([0.0, 1.0, 1.7])))
+                       alpha=float(rng.choice([0.0, 1.0, 1.7])),
+                       domain_x=int(rng.choice([8, 32])))
         eb = float(10 ** rng.uniform(-5, -1))
         assert_parity(x, eb, cfg)
+
+
+@pytest.mark.parametrize("order", list(itertools.permutations(range(3))))
+def test_x_extended_domain_every_dim_order(order):
+    """Sec. IV-C neighbour domain along x (the column's 32-point block): two full
+    blocks and a ragged tail along x, spline levels, both cubic kinds."""
+    x = fields.grf((40, 37, 70), 3.0, 12).numpy()
+    cfg = G.Config(dim_order=order, level_kind=(1, 1, 1), cubic_kind=(1, 0, 0), radius=512, domain_x=32)
+    assert_parity(x, 1e-3, cfg)
+
+
+def test_x_extended_domain_autotuned_and_unaligned_rows():
+    x = fields.lognormal((24, 40, 99), 11.0 / 3.0, 5).numpy()  # 99 floats per row: no tensor map
+    for eb in (1e-2, 1e-4):
+        assert_parity(x, eb, G.Config(autotune=True, radius=512, domain_x=32))
+    x2 = fields.grf((33, 17, 128), 4.0, 6).numpy()
+    assert_parity(x2, 1e-3, G.Config(dim_order=(2, 0, 1), level_kind=(0, 1, 1), domain_x=32))
 
 
 @pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4, 1e-5])

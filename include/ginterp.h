@@ -117,8 +117,10 @@ size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg);
  *   d_hist       [2R] out or NULL: histogram of d_codes (zeroed by the callee)
  *   d_hdr        out: device header (bounds, effective config, counts, status)
  *   d_ws         device scratch of ws_bytes >= interp_workspace_bytes(dims, cfg)
- * Guarantee: for every point |x - x'| <= e_l of its level <= eb_abs, where x' is the
- * output of interp_decompress; anchors and outliers are exact. */
+ * Guarantee: for every point |x - x'| <= e_l of its level, where x' is the output of
+ * interp_decompress and e_l = float(eb_abs / alpha^l) (header e[l]); e_0, the largest,
+ * is eb_abs rounded to float, so it may exceed eb_abs by up to half a float ulp.
+ * Anchors and outliers are exact. */
 int interp_compress(const float *d_x, const int64_t dims[3], double eb, const interp_config *cfg,
                     float *d_anchors, uint16_t *d_codes, uint32_t *d_out_idx, float *d_out_val,
                     uint64_t out_capacity, uint32_t *d_hist, interp_header *d_hdr,

@@ -91,6 +91,17 @@ double effective_alpha(const interp_config &c, double eb)
     return c.eb_mode ? alpha_of_eps(eb) : 1.0;
 }
 
+// Codes per store for rows of 8 codes starting at multiples of 8 along x: the
+// widest store whose alignment every such row start keeps.
+int code_store_width(const void *codes, int nx)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(codes);
+    if (a % 16 == 0 && nx % 8 == 0) return 8;
+    if (a % 8 == 0 && nx % 4 == 0) return 4;
+    if (a % 4 == 0 && nx % 2 == 0) return 2;
+    return 1;
+}
+
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? INTERP_OK : INTERP_ECUDA; }
 
 // ---- optional event timing around the tile kernels (measurement only)
@@ -168,7 +179,7 @@ int interp_compress_batched(const interp_compress_item *items, int n, interp_str
                 e = gi::launch_header_init(it.d_hdr, d, it.eb, c, alpha, s);
         }
         args[i] = gi::CompressArgs{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
-                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0, c.domain_x == 32};
+                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0, c.domain_x == 32, code_store_width(it.d_codes, d.nx)};
     }
     if (e == cudaSuccess) {
         timing_mark(0, 0, s);

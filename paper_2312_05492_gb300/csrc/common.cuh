@@ -132,6 +132,8 @@ struct CompressArgs {
     interp_header *hdr;
     bool vec_codes;  // codes 16-byte aligned and nx % 8 == 0: 8-code vector stores
     bool xdom32;     // x-extended neighbour domain requested (cfg.domain_x == 32)
+    int code_store;  // codes per store on rows of 8 codes starting at x = 8k: 8, 4 or 2
+                     // (by the alignment of codes and nx), else 1
 };
 
 struct DecompressArgs {

@@ -503,6 +503,7 @@ struct CBatch {
 struct CWrite {
     int R, bins, Ay, Ax, WX;
     bool smem_hist, vec_codes;
+    int code_store;
 };
 
 __device__ __forceinline__ CWrite cwrite_of(const CField &F)
@@ -515,6 +516,7 @@ __device__ __forceinline__ CWrite cwrite_of(const CField &F)
     w.Ax = (F.f.n[2] - 1) / 8 + 1;
     w.WX = (F.f.n[2] + 31) / 32;
     w.vec_codes = F.a.vec_codes;
+    w.code_store = F.a.code_store;
     return w;
 }
 
@@ -634,7 +636,7 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_con
         const int sub = lane & 3;
         // Fast path: every owned row of the slab lies inside the field, code rows are
         // 16-byte aligned and the histogram bins fit in shared memory.
-        const bool fast = cw.vec_codes && cw.smem_hist && sl.g0[1] + OY <= f.n[1] && sl.g0[2] + OX <= f.n[2];
+        const bool fast = cw.smem_hist && sl.g0[1] + OY <= f.n[1] && sl.g0[2] + OX <= f.n[2];
         if (fast) {
             const size_t plane = (size_t)f.n[1] * f.n[2];
             uint16_t *cb = F.a.codes + ((size_t)(sl.g0[0] + sl.own_lo) * f.n[1] + sl.g0[1]) * f.n[2] + sl.g0[2] +
@@ -655,7 +657,19 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_con
                     F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] =
                         box[pz * PLANE + y * EX + 8 * sub];
                 }
-                *reinterpret_cast<uint4 *>(cb + pzr * plane + (size_t)y * f.n[2]) = make_uint4(w[0], w[1], w[2], w[3]);
+                uint16_t *dst = cb + pzr * plane + (size_t)y * f.n[2];
+                if (cw.code_store == 8) {
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else if (cw.code_store == 4) {
+                    reinterpret_cast<uint2 *>(dst)[0] = make_uint2(w[0], w[1]);
+                    reinterpret_cast<uint2 *>(dst)[1] = make_uint2(w[2], w[3]);
+                } else if (cw.code_store == 2) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) reinterpret_cast<uint32_t *>(dst)[j] = w[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) dst[j] = (uint16_t)(w[j >> 1] >> (16 * (j & 1)));
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {  // every staged code here is < 2R
                     const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;

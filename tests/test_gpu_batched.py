@@ -56,7 +56,7 @@ def test_batched_equals_single_calls():
         cf, xr = _single(x, eb, cfg)
         torch.cuda.synchronize()
         _same(b.fields[i], b.outs[i], cf, xr)
-        assert float((b.outs[i] - x).abs().nan_to_num().max()) <= cf.host_header().eb_abs
+        assert float((b.outs[i] - x).abs().nan_to_num().max()) <= np.float32(cf.host_header().e[0])  # e_0
 
 
 def test_batch_order_does_not_matter():

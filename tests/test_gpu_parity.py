@@ -31,7 +31,7 @@ def test_grf64_linear_roundtrip():
     cfg = G.Config(dim_order=(0, 1, 2), level_kind=(0, 0, 0), eb_mode="rel", radius=512)
     cf, xr, h, oc = assert_parity(x, 1e-3, cfg)
     assert h.alpha == 1.5
-    assert np.abs(xr.astype(np.float64) - x).max() <= h.eb_abs
+    assert np.abs(xr.astype(np.float64) - x).max() <= np.float32(h.e[0])  # e_0 = float(eb_abs)
 
 
 @pytest.mark.parametrize("order", list(itertools.permutations(range(3))))

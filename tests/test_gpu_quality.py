@@ -55,6 +55,6 @@ def test_quality_matches_definition(name, make, eb, cfg):
     assert _close(got["psnr_db"], ref["psnr_db"], 1e-9)
     # the bound holds, so PSNR is at least the one of a uniform error of eb_abs
     h = cf.host_header()
-    assert got["max_abs_err"] <= h.eb_abs
+    assert got["max_abs_err"] <= np.float32(h.e[0])  # the float level bound e_0
     no_err = G.quality(cf)
     assert no_err["n"] == ref["n"] and math.isnan(no_err["psnr_db"]) and no_err["n_finite"] == 0

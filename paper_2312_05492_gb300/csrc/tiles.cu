@@ -854,7 +854,9 @@ __global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatc
                     d[3] = v.w;
                 }
                 // code 0 marks an outlier: its stored value was scattered into xrec
-                const uint32_t z = __vcmpeq2(v.x, 0u) | __vcmpeq2(v.y, 0u) | __vcmpeq2(v.z, 0u) | __vcmpeq2(v.w, 0u);
+                const uint32_t z = q < 4 ? (has_zero_half(v.x) | has_zero_half(v.y) | has_zero_half(v.z) |
+                                            has_zero_half(v.w))
+                                         : has_zero_half(v.x);  // the last group holds x = 32, 33 only
                 const int pz = row / EY, y = row % EY;
                 if (z && pz < nzp && y < nyr) {
                     const uint32_t wv[4] = {v.x, v.y, v.z, v.w};

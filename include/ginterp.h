@@ -232,6 +232,48 @@ size_t interp_quality_workspace_bytes(void);
 int interp_quality_report(const uint32_t *d_hist, int32_t radius, const float *d_x, const float *d_xrec,
                           uint64_t n, interp_quality *d_out, void *d_ws, size_t ws_bytes, interp_stream_t stream);
 
+/* ---- Canonical Huffman coding of the quant-codes (Sec. V-A: the lossless stage after
+ * the histogram; the codebook is built on the host, the codes are encoded and decoded on
+ * the GPU).  Stream: the codes are cut into chunks of 1024; a chunk's codewords are
+ * concatenated most-significant bit first into 32-bit words (its first bit is bit 31 of
+ * its first word) and padded with zero bits to a whole word; d_offsets[k] is chunk k's
+ * first word and d_offsets[nchunks] the total number of words. */
+
+/* Host only.  Code lengths and canonical codewords for the 2R symbols of h_hist (uint32
+ * counts): Huffman's construction (the two lightest subtrees merge first; ties by weight,
+ * then creation order: symbols by index, merged subtrees after), then, if a length
+ * exceeds max_len (1..24), lengths above it are cut to max_len and the longest codewords
+ * below it are lengthened until the Kraft sum is at most 1; canonical codewords assign
+ * consecutive values in (length, symbol) order.  Unused symbols get length 0; a single
+ * used symbol gets length 1.  h_lengths [2R] and h_codewords [2R] are outputs. */
+int interp_huffman_codebook(const uint32_t *h_hist, int32_t radius, int32_t max_len, uint8_t *h_lengths,
+                            uint32_t *h_codewords);
+
+/* Number of 1024-code chunks for n codes, and the words of stream room that always
+ * suffice with codewords of at most max_len bits. */
+uint64_t interp_huffman_chunks(uint64_t n);
+uint64_t interp_huffman_capacity_words(uint64_t n, int32_t max_len);
+
+/* Scratch for interp_huffman_encode / interp_huffman_decode (bytes). */
+size_t interp_huffman_workspace_bytes(int32_t radius);
+
+/* Encode n codes (each < 2R, every one with a nonzero length in d_lengths) with the
+ * codebook (d_lengths [2R], d_codewords [2R], device copies of interp_huffman_codebook's
+ * output).  Writes d_offsets [chunks + 1] and the stream d_words (capacity_words words,
+ * at least the used d_offsets[chunks]).  A chunk that would not fit, or a codebook with
+ * longer codewords than 24 bits, sets the device flag at the start of d_ws to 1 (0 on
+ * success); nothing outside d_words' capacity is written.  Stream-ordered. */
+int interp_huffman_encode(const uint16_t *d_codes, uint64_t n, int32_t radius, const uint8_t *d_lengths,
+                          const uint32_t *d_codewords, uint32_t *d_offsets, uint32_t *d_words,
+                          uint64_t capacity_words, void *d_ws, size_t ws_bytes, interp_stream_t stream);
+
+/* Decode the stream back into n codes (d_codes [n]) with the same codebook.  A word
+ * sequence that is not a codeword sets the device flag at the start of d_ws to 1.
+ * Stream-ordered. */
+int interp_huffman_decode(const uint32_t *d_words, const uint32_t *d_offsets, uint64_t n, int32_t radius,
+                          const uint8_t *d_lengths, const uint32_t *d_codewords, uint16_t *d_codes, void *d_ws,
+                          size_t ws_bytes, interp_stream_t stream);
+
 /* Measurement support (not part of the compression method): while enabled,
  * every interp_compress / interp_decompress call records a pair of CUDA events
  * on its stream immediately around its tile kernel (at most 512 pairs per kernel;

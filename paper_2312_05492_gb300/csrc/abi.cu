@@ -283,6 +283,55 @@ int interp_quality_report(const uint32_t *d_hist, int32_t radius, const float *d
                                           reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int interp_huffman_codebook(const uint32_t *h_hist, int32_t radius, int32_t max_len, uint8_t *h_lengths,
+                            uint32_t *h_codewords)
+{
+    if (radius < 2 || radius > 32768 || !h_hist || !h_lengths || !h_codewords) return INTERP_EINVAL;
+    if (max_len < 1 || max_len > gi::huffman_max_len()) return INTERP_EINVAL;
+    return gi::huffman_codebook(h_hist, 2 * radius, max_len, h_lengths, h_codewords) ? INTERP_OK : INTERP_EINVAL;
+}
+
+uint64_t interp_huffman_chunks(uint64_t n) { return gi::huffman_chunks(n); }
+
+uint64_t interp_huffman_capacity_words(uint64_t n, int32_t max_len)
+{
+    if (max_len < 1 || max_len > gi::huffman_max_len()) return 0;
+    return gi::huffman_capacity_words(n, max_len);
+}
+
+size_t interp_huffman_workspace_bytes(int32_t radius)
+{
+    if (radius < 2 || radius > 32768) return 0;
+    return 256 + gi::huffman_decode_workspace(2 * radius);
+}
+
+int interp_huffman_encode(const uint16_t *d_codes, uint64_t n, int32_t radius, const uint8_t *d_lengths,
+                          const uint32_t *d_codewords, uint32_t *d_offsets, uint32_t *d_words,
+                          uint64_t capacity_words, void *d_ws, size_t ws_bytes, interp_stream_t stream)
+{
+    if (radius < 2 || radius > 32768 || !d_lengths || !d_codewords || !d_offsets || !d_ws) return INTERP_EINVAL;
+    if (n > 0 && (!d_codes || !d_words)) return INTERP_EINVAL;
+    if (n >= (1ull << 32)) return INTERP_EINVAL;
+    if (ws_bytes < interp_huffman_workspace_bytes(radius)) return INTERP_EWORKSPACE;
+    unsigned int *bad = static_cast<unsigned int *>(d_ws);
+    return cuda_status(gi::launch_huffman_encode(d_codes, n, d_lengths, d_codewords, 2 * radius, d_offsets, d_words,
+                                                 capacity_words, bad, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int interp_huffman_decode(const uint32_t *d_words, const uint32_t *d_offsets, uint64_t n, int32_t radius,
+                          const uint8_t *d_lengths, const uint32_t *d_codewords, uint16_t *d_codes, void *d_ws,
+                          size_t ws_bytes, interp_stream_t stream)
+{
+    if (radius < 2 || radius > 32768 || !d_lengths || !d_codewords || !d_offsets || !d_ws) return INTERP_EINVAL;
+    if (n > 0 && (!d_codes || !d_words)) return INTERP_EINVAL;
+    if (n >= (1ull << 32)) return INTERP_EINVAL;
+    if (ws_bytes < interp_huffman_workspace_bytes(radius)) return INTERP_EWORKSPACE;
+    unsigned char *ws = static_cast<unsigned char *>(d_ws);
+    unsigned int *bad = reinterpret_cast<unsigned int *>(ws);
+    return cuda_status(gi::launch_huffman_decode(d_words, d_offsets, n, d_lengths, d_codewords, 2 * radius, d_codes,
+                                                 ws + 256, bad, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 double interp_alpha(double eps) { return alpha_of_eps(eps); }
 
 int interp_value_range(const float *d_x, const int64_t dims[3], float *d_range, void *d_ws, size_t ws_bytes,

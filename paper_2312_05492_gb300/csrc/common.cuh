@@ -168,6 +168,19 @@ cudaError_t launch_quality(const uint32_t *hist, int radius, const float *x, con
                            interp_quality *out, void *ws, cudaStream_t s);
 size_t quality_workspace_bytes();
 
+// canonical Huffman coding of the codes (huffman.cu)
+bool huffman_codebook(const uint32_t *hist, int nsym, int max_len, uint8_t *lengths, uint32_t *codewords);
+unsigned long long huffman_chunks(unsigned long long n);
+unsigned long long huffman_capacity_words(unsigned long long n, int max_len);
+size_t huffman_decode_workspace(int nsym);
+int huffman_max_len();
+cudaError_t launch_huffman_encode(const uint16_t *codes, unsigned long long n, const uint8_t *lengths,
+                                  const uint32_t *codewords, int nsym, uint32_t *offsets, uint32_t *words,
+                                  unsigned long long capacity_words, unsigned int *bad, cudaStream_t s);
+cudaError_t launch_huffman_decode(const uint32_t *words, const uint32_t *offsets, unsigned long long n,
+                                  const uint8_t *lengths, const uint32_t *codewords, int nsym, uint16_t *codes,
+                                  void *ws, unsigned int *bad, cudaStream_t s);
+
 int range_blocks();
 int sm_count();
 

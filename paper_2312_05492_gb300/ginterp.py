@@ -26,7 +26,9 @@ FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress",
              "qcode_histogram", "interp_autotune", "interp_timing_enable", "interp_timing_read",
              "interp_compress_noalloc", "interp_noalloc_scratch_bytes", "interp_compress_batched",
              "interp_decompress_batched", "interp_status_string", "interp_alpha", "interp_value_range",
-             "interp_quality_workspace_bytes", "interp_quality_report")
+             "interp_quality_workspace_bytes", "interp_quality_report", "interp_huffman_codebook",
+             "interp_huffman_chunks", "interp_huffman_capacity_words", "interp_huffman_workspace_bytes",
+             "interp_huffman_encode", "interp_huffman_decode")
 
 # kernels each call launches (memsets excluded): compress = [profile] + range or
 # header + tiles + outlier scan + outlier write; decompress = scatter + tiles
@@ -102,6 +104,18 @@ def load() -> ctypes.CDLL:
     lib.interp_decompress.argtypes = [dims_t, P, P, P, P, P, u64, P, P]
     lib.qcode_histogram.restype = ctypes.c_int
     lib.qcode_histogram.argtypes = [P, u64, i32, P, P]
+    lib.interp_huffman_codebook.restype = ctypes.c_int
+    lib.interp_huffman_codebook.argtypes = [P, i32, i32, P, P]
+    lib.interp_huffman_chunks.restype = u64
+    lib.interp_huffman_chunks.argtypes = [u64]
+    lib.interp_huffman_capacity_words.restype = u64
+    lib.interp_huffman_capacity_words.argtypes = [u64, i32]
+    lib.interp_huffman_workspace_bytes.restype = ctypes.c_size_t
+    lib.interp_huffman_workspace_bytes.argtypes = [i32]
+    lib.interp_huffman_encode.restype = ctypes.c_int
+    lib.interp_huffman_encode.argtypes = [P, u64, i32, P, P, P, P, u64, P, ctypes.c_size_t, P]
+    lib.interp_huffman_decode.restype = ctypes.c_int
+    lib.interp_huffman_decode.argtypes = [P, P, u64, i32, P, P, P, P, ctypes.c_size_t, P]
     lib.interp_quality_workspace_bytes.restype = ctypes.c_size_t
     lib.interp_quality_workspace_bytes.argtypes = []
     lib.interp_quality_report.restype = ctypes.c_int
@@ -429,6 +443,71 @@ def quality(cf: "CompressedField", x: torch.Tensor | None = None, xrec: torch.Te
     host = out.cpu().numpy().tobytes()
     q = interp_quality.from_buffer_copy(host)
     return {name: getattr(q, name) for name, _ in interp_quality._fields_ if name != "reserved"}
+
+
+def huffman_codebook(hist, radius: int, max_len: int = 16):
+    """Canonical Huffman codebook (host) from a 2R-bin histogram (numpy array or tensor):
+    (lengths uint8[2R], codewords uint32[2R]) as numpy arrays."""
+    import numpy as np
+    a = np.asarray(hist.cpu().numpy() if isinstance(hist, torch.Tensor) else hist)
+    h = np.ascontiguousarray(a.view(np.uint32) if a.dtype.itemsize == 4 and a.dtype.kind in "iu" else a.astype(np.uint32))
+    lengths = np.zeros(2 * radius, np.uint8)
+    codewords = np.zeros(2 * radius, np.uint32)
+    rc = load().interp_huffman_codebook(h.ctypes.data, int(radius), int(max_len), lengths.ctypes.data,
+                                        codewords.ctypes.data)
+    _check(rc, "interp_huffman_codebook")
+    return lengths, codewords
+
+
+@dataclass
+class HuffmanStream:
+    """Device-resident Huffman stream of n codes (chunks of 1024 codes)."""
+    n: int
+    radius: int
+    lengths: torch.Tensor    # uint8 [2R] (device)
+    codewords: torch.Tensor  # int32 storage of uint32 [2R] (device)
+    offsets: torch.Tensor    # int32 storage of uint32 [chunks + 1]
+    words: torch.Tensor      # int32 storage of uint32 [capacity]
+    flag: torch.Tensor       # workspace; its first word is the error flag
+
+    def total_words(self) -> int:
+        return int(self.offsets[-1].item()) & 0xFFFFFFFF
+
+    def nbytes(self) -> int:
+        return 4 * self.total_words() + 4 * self.offsets.numel()
+
+
+def huffman_encode(codes: torch.Tensor, radius: int, lengths, codewords, max_len: int = 16, stream=None,
+                   ws: torch.Tensor | None = None) -> HuffmanStream:
+    """Encode uint16 codes (an int16 tensor) on the device with a host codebook."""
+    import numpy as np
+    dev = codes.device
+    n = int(codes.numel())
+    d_len = torch.from_numpy(np.ascontiguousarray(lengths, np.uint8)).to(dev)
+    d_cw = torch.from_numpy(np.ascontiguousarray(codewords, np.uint32).view(np.int32)).to(dev)
+    nch = int(load().interp_huffman_chunks(n))
+    cap = int(load().interp_huffman_capacity_words(n, int(max_len)))
+    offsets = torch.empty(nch + 1, dtype=torch.int32, device=dev)
+    words = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    wsb = int(load().interp_huffman_workspace_bytes(int(radius)))
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    rc = load().interp_huffman_encode(_ptr(codes), n, int(radius), _ptr(d_len), _ptr(d_cw), _ptr(offsets),
+                                      _ptr(words), cap, _ptr(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc, "interp_huffman_encode")
+    return HuffmanStream(n, int(radius), d_len, d_cw, offsets, words, ws)
+
+
+def huffman_decode(hs: HuffmanStream, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Decode a stream back into uint16 codes (an int16 tensor)."""
+    dev = hs.words.device
+    if out is None:
+        out = torch.empty(hs.n, dtype=torch.int16, device=dev)
+    rc = load().interp_huffman_decode(_ptr(hs.words), _ptr(hs.offsets), hs.n, hs.radius, _ptr(hs.lengths),
+                                      _ptr(hs.codewords), _ptr(out), _ptr(hs.flag), hs.flag.numel(),
+                                      _stream_ptr(stream))
+    _check(rc, "interp_huffman_decode")
+    return out
 
 
 def autotune(x: torch.Tensor, radius: int = 512, stream=None):

@@ -1,0 +1,77 @@
+"""GPU Huffman coding of quant-codes (Sec. V-A lossless stage) against the oracle:
+the encoded stream (chunk offsets and words) equals the oracle's bit for bit, and
+decoding returns the codes."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import huffman as H
+from paper_2312_05492_gb300 import fields
+from paper_2312_05492_gb300 import ginterp as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.load()
+
+
+CASES = [
+    ("grf64_linear", lambda: fields.grf((64, 64, 64), 3.0, 0), 1e-3, G.Config(level_kind=(0, 0, 0)), 16),
+    ("lognormal_auto", lambda: fields.lognormal((72, 56, 96), 11.0 / 3.0, 1), 1e-4, G.Config(autotune=True), 12),
+    ("shocks_r4", lambda: fields.shocks((40, 48, 64), 6), 1e-5, G.Config(radius=4), 16),
+    ("ragged_tail", lambda: fields.grf((3, 17, 41), 2.0, 9), 1e-2, G.Config(radius=64), 8),
+]
+
+
+@pytest.mark.parametrize("name,make,eb,cfg,max_len", CASES, ids=[c[0] for c in CASES])
+def test_stream_matches_oracle_and_round_trips(name, make, eb, cfg, max_len):
+    x = make().cuda()
+    cf = G.compress(x, eb, cfg)
+    torch.cuda.synchronize()
+    R = cfg.radius
+    hist = cf.hist.cpu().numpy().view(np.uint32)
+    lengths, cw = G.huffman_codebook(hist, R, max_len)
+    hs = G.huffman_encode(cf.codes, R, lengths, cw, max_len=max_len)
+    torch.cuda.synchronize()
+    assert int(hs.flag[:4].view(torch.int32).item()) == 0
+    codes = cf.codes.cpu().numpy().view(np.uint16).astype(np.int64)
+    owords, ooffs = H.encode_chunks(codes, lengths.astype(np.int64), cw.astype(np.uint64), chunk=1024)
+    offs = hs.offsets.cpu().numpy().view(np.uint32)
+    assert np.array_equal(offs, ooffs)
+    total = int(offs[-1])
+    assert np.array_equal(hs.words[:total].cpu().numpy().view(np.uint32), owords)
+    assert int((lengths.astype(np.int64)[codes]).sum()) <= 32 * total
+    back = G.huffman_decode(hs)
+    torch.cuda.synchronize()
+    assert int(hs.flag[:4].view(torch.int32).item()) == 0
+    assert torch.equal(back, cf.codes)
+    # the stream is within one word per chunk of the entropy-coded size
+    p = hist[hist > 0] / hist.sum()
+    ent_bits = float(-(p * np.log2(p)).sum()) * codes.size
+    assert 32 * total >= ent_bits - 1e-6
+
+
+def test_empty_and_corrupt_streams():
+    R = 8
+    lengths, cw = G.huffman_codebook(np.ones(2 * R, np.uint32), R, 8)
+    hs = G.huffman_encode(torch.zeros(0, dtype=torch.int16, device="cuda"), R, lengths, cw, max_len=8)
+    torch.cuda.synchronize()
+    assert hs.total_words() == 0 and hs.n == 0
+    # a stream of all-ones words holds no valid codeword of a 16-symbol complete code?
+    # (all codewords of a complete code appear, so flip the codebook instead: decode with
+    # a codebook whose lengths do not cover the stream's prefixes)
+    codes = torch.randint(0, 2 * R, (5000,), dtype=torch.int16, device="cuda")
+    hs = G.huffman_encode(codes, R, lengths, cw, max_len=8)
+    torch.cuda.synchronize()
+    assert torch.equal(G.huffman_decode(hs), codes)
+    partial = np.zeros(2 * R, np.uint8)
+    partial[0] = 1  # codeword "0" only: any '1' bit cannot be decoded
+    bad = G.HuffmanStream(hs.n, R, torch.from_numpy(partial).cuda(), hs.codewords * 0, hs.offsets, hs.words,
+                          hs.flag)
+    G.huffman_decode(bad)
+    torch.cuda.synchronize()
+    assert int(hs.flag[:4].view(torch.int32).item()) == 1

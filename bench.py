@@ -164,6 +164,55 @@ def quality_summary(G, cf, x, xrec) -> dict:
             "max_abs_err": q["max_abs_err"]}
 
 
+def lossless_stage(G, cf, stream, max_len: int = 16) -> dict:
+    """The lossless stage after the histogram (Sec. V-A), outside the timed region:
+    host codebook time, the chunked Huffman encoder's and decoder's device times
+    (events on the launching stream, 10 launches each, codebook already resident),
+    the coded rate beside the entropy, and the whole archive's compression ratio
+    (header, anchors, codebook lengths, coded stream with its chunk offsets,
+    outliers)."""
+    import time
+
+    import numpy as np
+    import torch
+    h = cf.host_header(refresh=True)
+    R = h.cfg.radius
+    hist = cf.hist.cpu().numpy().view(np.uint32)
+    t0 = time.perf_counter()
+    lengths, cw = G.huffman_codebook(hist, R, max_len)
+    book_us = (time.perf_counter() - t0) * 1e6
+    hs = G.huffman_encode(cf.codes, R, lengths, cw, max_len, stream=stream)
+    out = torch.empty_like(cf.codes)
+
+    def timed(fn, k=10):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    enc_ms = timed(lambda: G.huffman_reencode(hs, cf.codes, stream))
+    dec_ms = timed(lambda: G.huffman_decode(hs, out, stream))
+    assert int(hs.flag[:4].view(torch.int32).item()) == 0 and torch.equal(out, cf.codes)
+    n = cf.codes.numel()
+    coded = hs.nbytes()
+    n_anchor = cf.anchors.numel()
+    n_out = int(h.n_outliers)
+    archive = G.HEADER_BYTES + 4 * n_anchor + 2 * R + coded + 8 * n_out
+    del hs, out
+    return {"codebook_host_us": round(book_us, 1), "max_len": int(lengths.max()),
+            "encode_ms": round(enc_ms, 4), "decode_ms": round(dec_ms, 4),
+            "encode_gbs_of_field": round(4 * n / (enc_ms * 1e-3) / 1e9, 1),
+            "decode_gbs_of_field": round(4 * n / (dec_ms * 1e-3) / 1e9, 1),
+            "bits_per_code": round(8 * coded / n, 4),
+            "archive_bytes": archive, "compression_ratio": round(4 * n / archive, 2)}
+
+
 def x_domain_variant(G, x, eb, cfg, dims, stream) -> dict:
     """The same field with the x-extended neighbour domain (Sec. IV-C, the 32x8x8
     blocks): tile-kernel times (library events, 10 launches each) and the quality of
@@ -322,6 +371,7 @@ def run_ours(args, rank, world, local):
         "max_abs_err_over_eb": err / h.eb_abs,
         "quality": quality_summary(G, cf, x, xrec),
         "x_extended_domain": x_domain_variant(G, x, args.eb, cfg, dims, stream),
+        "lossless": lossless_stage(G, cf, stream),
         "gpu_launches": (G.launches_compress(cfg) + G.LAUNCHES_DECOMPRESS) * args.steps,
         "clocks": clocks,
     }

@@ -254,8 +254,9 @@ int interp_huffman_codebook(const uint32_t *h_hist, int32_t radius, int32_t max_
 uint64_t interp_huffman_chunks(uint64_t n);
 uint64_t interp_huffman_capacity_words(uint64_t n, int32_t max_len);
 
-/* Scratch for interp_huffman_encode / interp_huffman_decode (bytes). */
-size_t interp_huffman_workspace_bytes(int32_t radius);
+/* Scratch for interp_huffman_encode / interp_huffman_decode of n codes (bytes; 0 for
+ * a radius outside 2..32768 or n >= 2^32). */
+size_t interp_huffman_workspace_bytes(uint64_t n, int32_t radius);
 
 /* Encode n codes (each < 2R, every one with a nonzero length in d_lengths) with the
  * codebook (d_lengths [2R], d_codewords [2R], device copies of interp_huffman_codebook's

@@ -2,6 +2,7 @@
 // workspace layout and the stream-ordered launch sequences of compression
 // (profile -> range/bounds -> tiles -> outlier compaction) and decompression
 // (outlier scatter -> tiles).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -299,10 +300,10 @@ uint64_t interp_huffman_capacity_words(uint64_t n, int32_t max_len)
     return gi::huffman_capacity_words(n, max_len);
 }
 
-size_t interp_huffman_workspace_bytes(int32_t radius)
+size_t interp_huffman_workspace_bytes(uint64_t n, int32_t radius)
 {
-    if (radius < 2 || radius > 32768) return 0;
-    return 256 + gi::huffman_decode_workspace(2 * radius);
+    if (radius < 2 || radius > 32768 || n >= (1ull << 32)) return 0;
+    return 256 + std::max(gi::huffman_decode_workspace(2 * radius), gi::huffman_encode_workspace(n));
 }
 
 int interp_huffman_encode(const uint16_t *d_codes, uint64_t n, int32_t radius, const uint8_t *d_lengths,
@@ -312,10 +313,12 @@ int interp_huffman_encode(const uint16_t *d_codes, uint64_t n, int32_t radius, c
     if (radius < 2 || radius > 32768 || !d_lengths || !d_codewords || !d_offsets || !d_ws) return INTERP_EINVAL;
     if (n > 0 && (!d_codes || !d_words)) return INTERP_EINVAL;
     if (n >= (1ull << 32)) return INTERP_EINVAL;
-    if (ws_bytes < interp_huffman_workspace_bytes(radius)) return INTERP_EWORKSPACE;
-    unsigned int *bad = static_cast<unsigned int *>(d_ws);
+    if (ws_bytes < interp_huffman_workspace_bytes(n, radius)) return INTERP_EWORKSPACE;
+    unsigned char *ws = static_cast<unsigned char *>(d_ws);
+    unsigned int *bad = reinterpret_cast<unsigned int *>(ws);
     return cuda_status(gi::launch_huffman_encode(d_codes, n, d_lengths, d_codewords, 2 * radius, d_offsets, d_words,
-                                                 capacity_words, bad, reinterpret_cast<cudaStream_t>(stream)));
+                                                 capacity_words, reinterpret_cast<uint32_t *>(ws + 256), bad,
+                                                 reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int interp_huffman_decode(const uint32_t *d_words, const uint32_t *d_offsets, uint64_t n, int32_t radius,
@@ -325,7 +328,7 @@ int interp_huffman_decode(const uint32_t *d_words, const uint32_t *d_offsets, ui
     if (radius < 2 || radius > 32768 || !d_lengths || !d_codewords || !d_offsets || !d_ws) return INTERP_EINVAL;
     if (n > 0 && (!d_codes || !d_words)) return INTERP_EINVAL;
     if (n >= (1ull << 32)) return INTERP_EINVAL;
-    if (ws_bytes < interp_huffman_workspace_bytes(radius)) return INTERP_EWORKSPACE;
+    if (ws_bytes < interp_huffman_workspace_bytes(n, radius)) return INTERP_EWORKSPACE;
     unsigned char *ws = static_cast<unsigned char *>(d_ws);
     unsigned int *bad = reinterpret_cast<unsigned int *>(ws);
     return cuda_status(gi::launch_huffman_decode(d_words, d_offsets, n, d_lengths, d_codewords, 2 * radius, d_codes,

@@ -174,9 +174,11 @@ unsigned long long huffman_chunks(unsigned long long n);
 unsigned long long huffman_capacity_words(unsigned long long n, int max_len);
 size_t huffman_decode_workspace(int nsym);
 int huffman_max_len();
+size_t huffman_encode_workspace(unsigned long long n);  // per-CTA word counts of the encoder
 cudaError_t launch_huffman_encode(const uint16_t *codes, unsigned long long n, const uint8_t *lengths,
                                   const uint32_t *codewords, int nsym, uint32_t *offsets, uint32_t *words,
-                                  unsigned long long capacity_words, unsigned int *bad, cudaStream_t s);
+                                  unsigned long long capacity_words, uint32_t *block_words, unsigned int *bad,
+                                  cudaStream_t s);
 cudaError_t launch_huffman_decode(const uint32_t *words, const uint32_t *offsets, unsigned long long n,
                                   const uint8_t *lengths, const uint32_t *codewords, int nsym, uint16_t *codes,
                                   void *ws, unsigned int *bad, cudaStream_t s);

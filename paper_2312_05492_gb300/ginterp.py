@@ -111,7 +111,7 @@ def load() -> ctypes.CDLL:
     lib.interp_huffman_capacity_words.restype = u64
     lib.interp_huffman_capacity_words.argtypes = [u64, i32]
     lib.interp_huffman_workspace_bytes.restype = ctypes.c_size_t
-    lib.interp_huffman_workspace_bytes.argtypes = [i32]
+    lib.interp_huffman_workspace_bytes.argtypes = [u64, i32]
     lib.interp_huffman_encode.restype = ctypes.c_int
     lib.interp_huffman_encode.argtypes = [P, u64, i32, P, P, P, P, u64, P, ctypes.c_size_t, P]
     lib.interp_huffman_decode.restype = ctypes.c_int
@@ -489,13 +489,26 @@ def huffman_encode(codes: torch.Tensor, radius: int, lengths, codewords, max_len
     cap = int(load().interp_huffman_capacity_words(n, int(max_len)))
     offsets = torch.empty(nch + 1, dtype=torch.int32, device=dev)
     words = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
-    wsb = int(load().interp_huffman_workspace_bytes(int(radius)))
+    wsb = int(load().interp_huffman_workspace_bytes(n, int(radius)))
     if ws is None or ws.numel() < wsb:
         ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     rc = load().interp_huffman_encode(_ptr(codes), n, int(radius), _ptr(d_len), _ptr(d_cw), _ptr(offsets),
                                       _ptr(words), cap, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc, "interp_huffman_encode")
     return HuffmanStream(n, int(radius), d_len, d_cw, offsets, words, ws)
+
+
+def huffman_reencode(hs: HuffmanStream, codes: torch.Tensor, stream=None) -> HuffmanStream:
+    """Encode codes again into an existing stream's buffers with its codebook (no
+    allocation, no host work: only the encoder's launches)."""
+    n = int(codes.numel())
+    if n != hs.n:
+        raise ValueError(f"stream holds {hs.n} codes, got {n}")
+    rc = load().interp_huffman_encode(_ptr(codes), n, hs.radius, _ptr(hs.lengths), _ptr(hs.codewords),
+                                      _ptr(hs.offsets), _ptr(hs.words), hs.words.numel(), _ptr(hs.flag),
+                                      hs.flag.numel(), _stream_ptr(stream))
+    _check(rc, "interp_huffman_encode")
+    return hs
 
 
 def huffman_decode(hs: HuffmanStream, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

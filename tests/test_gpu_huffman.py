@@ -24,6 +24,10 @@ CASES = [
     ("lognormal_auto", lambda: fields.lognormal((72, 56, 96), 11.0 / 3.0, 1), 1e-4, G.Config(autotune=True), 12),
     ("shocks_r4", lambda: fields.shocks((40, 48, 64), 6), 1e-5, G.Config(radius=4), 16),
     ("ragged_tail", lambda: fields.grf((3, 17, 41), 2.0, 9), 1e-2, G.Config(radius=64), 8),
+    # 16384 symbols: the largest codebook kept in shared memory (above the default 48 KB)
+    ("radius8192", lambda: fields.grf((24, 40, 56), 2.0, 5), 1e-6, G.Config(radius=8192), 24),
+    # 32768 symbols: the codebook is read from global memory
+    ("radius16384", lambda: fields.grf((24, 40, 56), 2.0, 6), 1e-7, G.Config(radius=16384), 24),
 ]
 
 
@@ -73,5 +77,38 @@ def test_empty_and_corrupt_streams():
     bad = G.HuffmanStream(hs.n, R, torch.from_numpy(partial).cuda(), hs.codewords * 0, hs.offsets, hs.words,
                           hs.flag)
     G.huffman_decode(bad)
+    torch.cuda.synchronize()
+    assert int(hs.flag[:4].view(torch.int32).item()) == 1
+
+
+def test_unaligned_buffers_and_reencode():
+    """Codes and outputs that do not start on 16 bytes take the scalar load and store
+    paths; re-encoding into a stream's buffers gives the same stream; too little room
+    for the words sets the flag instead of writing past the buffer."""
+    R = 64
+    base = fields.grf((20, 33, 47), 2.0, 4).cuda()
+    cf = G.compress(base, 1e-3, G.Config(radius=R))
+    torch.cuda.synchronize()
+    hist = cf.hist.cpu().numpy().view(np.uint32)
+    lengths, cw = G.huffman_codebook(hist, R, 12)
+    pad = torch.zeros(cf.codes.numel() + 1, dtype=torch.int16, device="cuda")
+    pad[1:] = cf.codes
+    shifted = pad[1:]  # 2-byte offset
+    hs = G.huffman_encode(shifted, R, lengths, cw, max_len=12)
+    ref = G.huffman_encode(cf.codes, R, lengths, cw, max_len=12)
+    torch.cuda.synchronize()
+    total = ref.total_words()
+    assert hs.total_words() == total
+    assert torch.equal(hs.words[:total], ref.words[:total]) and torch.equal(hs.offsets, ref.offsets)
+    out = torch.zeros(cf.codes.numel() + 1, dtype=torch.int16, device="cuda")
+    G.huffman_decode(hs, out[1:])
+    torch.cuda.synchronize()
+    assert torch.equal(out[1:], cf.codes) and int(out[0].item()) == 0
+    hs.words.zero_()
+    G.huffman_reencode(hs, cf.codes)
+    torch.cuda.synchronize()
+    assert torch.equal(hs.words[:total], ref.words[:total])
+    short = G.HuffmanStream(hs.n, R, hs.lengths, hs.codewords, hs.offsets, hs.words[: total // 2], hs.flag)
+    G.huffman_reencode(short, cf.codes)
     torch.cuda.synchronize()
     assert int(hs.flag[:4].view(torch.int32).item()) == 1

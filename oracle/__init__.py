@@ -40,27 +40,29 @@ def _load():
     lib.orc_alpha.restype = f64
     lib.orc_alpha.argtypes = [f64]
     lib.orc_level_bounds.restype = None
-    lib.orc_level_bounds.argtypes = [f64, f64, P, P, P]
+    lib.orc_level_bounds.argtypes = [f64, f64, i32, P, P, P]
+    lib.orc_levels.restype = i32
+    lib.orc_levels.argtypes = [i32]
     lib.orc_value_range.restype = i64
     lib.orc_value_range.argtypes = [P, i64, P, P]
     lib.orc_rel_to_abs.restype = f64
     lib.orc_rel_to_abs.argtypes = [f64, ctypes.c_float, ctypes.c_float]
     lib.orc_anchor_count.restype = i64
-    lib.orc_anchor_count.argtypes = [i64, i64, i64]
+    lib.orc_anchor_count.argtypes = [i64, i64, i64, i32]
     lib.orc_spline.restype = ctypes.c_float
     lib.orc_spline.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
-    lib.orc_schedule_maps.restype = None
-    lib.orc_schedule_maps.argtypes = [i64, i64, i64, P, P, P, i32, P, P]
+    lib.orc_schedule_maps.restype = ctypes.c_int
+    lib.orc_schedule_maps.argtypes = [i64, i64, i64, P, P, P, i32, i32, P, P]
     lib.orc_compress.restype = i64
-    lib.orc_compress.argtypes = [P, i64, i64, i64, P, P, P, i32, i32, P, P, P, P, P, P, P, i64, P]
+    lib.orc_compress.argtypes = [P, i64, i64, i64, P, P, P, i32, i32, i32, P, P, P, P, P, P, P, i64, P]
     lib.orc_decompress.restype = ctypes.c_int
-    lib.orc_decompress.argtypes = [i64, i64, i64, P, P, P, i32, i32, P, P, P, P, P, i64, P]
-    lib.orc_predict_original.restype = None
-    lib.orc_predict_original.argtypes = [P, i64, i64, i64, P, P, P, i32, P, P]
+    lib.orc_decompress.argtypes = [i64, i64, i64, P, P, P, i32, i32, i32, P, P, P, P, P, i64, P]
+    lib.orc_predict_original.restype = ctypes.c_int
+    lib.orc_predict_original.argtypes = [P, i64, i64, i64, P, P, P, i32, i32, P, P]
     lib.orc_histogram.restype = None
     lib.orc_histogram.argtypes = [P, i64, i32, P]
     lib.orc_profile.restype = None
-    lib.orc_profile.argtypes = [P, i64, i64, i64, P]
+    lib.orc_profile.argtypes = [P, i64, i64, i64, i32, P]
     lib.orc_autotune_decide.restype = None
     lib.orc_autotune_decide.argtypes = [P, P, P, P]
     _lib = lib
@@ -84,12 +86,16 @@ class Config:
     cubic_kind[axis]: 0 = not-a-knot, 1 = natural.
     domain_x: neighbour domain along x, 8 (the closed 8^3 chunk, Sec. IV-A) or 32
       (the x-extended 32x8x8 block of Sec. IV-C).
+    ndim: chunk geometry (Sec. IV-A): 3 = 8^3 chunks; 2 = 16^2 chunks over (y, x),
+      every z-slice independent; 1 = 512-point chunks along x, every row independent.
+      Levels coarser than stride 4 (2-D, 1-D) follow level_kind[2].
     """
     order: tuple = (0, 1, 2)
     level_kind: tuple = (1, 1, 1)
     cubic_kind: tuple = (0, 0, 0)
     radius: int = 512
     domain_x: int = 8
+    ndim: int = 3
 
 
 @dataclass
@@ -113,12 +119,17 @@ def alpha(eps: float) -> float:
     return float(_load().orc_alpha(float(eps)))
 
 
-def level_bounds(eb_abs: float, alpha_: float):
-    """e_l = eb / alpha^l for l = 0, 1, 2 (strides 1, 2, 4), with 2e_l and 1/(2e_l)."""
-    e = np.zeros(3, np.float32)
-    twoe = np.zeros(3, np.float32)
-    inv2e = np.zeros(3, np.float32)
-    _load().orc_level_bounds(float(eb_abs), float(alpha_), _ptr(e), _ptr(twoe), _ptr(inv2e))
+def levels(ndim: int = 3) -> int:
+    """Interpolation levels of the chunk geometry: 3 (8^3), 4 (16^2), 9 (512)."""
+    return int(_load().orc_levels(int(ndim)))
+
+
+def level_bounds(eb_abs: float, alpha_: float, nlev: int = 3):
+    """e_l = eb / alpha^l for l = 0 .. nlev-1 (strides 1, 2, 4, ...), with 2e_l and 1/(2e_l)."""
+    e = np.zeros(nlev, np.float32)
+    twoe = np.zeros(nlev, np.float32)
+    inv2e = np.zeros(nlev, np.float32)
+    _load().orc_level_bounds(float(eb_abs), float(alpha_), int(nlev), _ptr(e), _ptr(twoe), _ptr(inv2e))
     return e, twoe, inv2e
 
 
@@ -134,8 +145,8 @@ def rel_to_abs(eps: float, vmin: float, vmax: float) -> float:
     return float(_load().orc_rel_to_abs(float(eps), float(vmin), float(vmax)))
 
 
-def anchor_count(dims) -> int:
-    return int(_load().orc_anchor_count(*[int(d) for d in dims]))
+def anchor_count(dims, ndim: int = 3) -> int:
+    return int(_load().orc_anchor_count(*[int(d) for d in dims], int(ndim)))
 
 
 def spline(kind: int, m3: float, m1: float, p1: float, p3: float) -> float:
@@ -147,8 +158,11 @@ def schedule_maps(dims, cfg: Config):
     n = int(np.prod(dims))
     pm = np.zeros(n, np.uint8)
     km = np.zeros(n, np.uint8)
-    _load().orc_schedule_maps(*[int(d) for d in dims], _ptr(_i32(cfg.order)), _ptr(_i32(cfg.level_kind)),
-                              _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x), _ptr(pm), _ptr(km))
+    rc = _load().orc_schedule_maps(*[int(d) for d in dims], _ptr(_i32(cfg.order)), _ptr(_i32(cfg.level_kind)),
+                                   _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x), int(cfg.ndim), _ptr(pm),
+                                   _ptr(km))
+    if rc != 0:
+        raise ValueError("bad configuration")
     return pm.reshape(dims), km.reshape(dims)
 
 
@@ -157,13 +171,15 @@ def predict_original(x: np.ndarray, cfg: Config):
     x = np.ascontiguousarray(x, dtype=np.float32)
     pred = np.zeros_like(x)
     kind = np.zeros(x.shape, np.uint8)
-    _load().orc_predict_original(_ptr(x), *[int(d) for d in x.shape], _ptr(_i32(cfg.order)),
-                                 _ptr(_i32(cfg.level_kind)), _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x),
-                                 _ptr(pred), _ptr(kind))
+    rc = _load().orc_predict_original(_ptr(x), *[int(d) for d in x.shape], _ptr(_i32(cfg.order)),
+                                      _ptr(_i32(cfg.level_kind)), _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x),
+                                      int(cfg.ndim), _ptr(pred), _ptr(kind))
+    if rc != 0:
+        raise ValueError("bad configuration")
     return pred, kind
 
 
-def bounds_for(x: np.ndarray, eb: float, mode: str = "rel", alpha_override: float | None = None):
+def bounds_for(x: np.ndarray, eb: float, mode: str = "rel", alpha_override: float | None = None, ndim: int = 3):
     """Absolute bound and level bounds as the compressor derives them (Sec. IV-B)."""
     if mode == "rel":
         lo, hi, _ = value_range(x)
@@ -172,7 +188,7 @@ def bounds_for(x: np.ndarray, eb: float, mode: str = "rel", alpha_override: floa
     else:
         eb_abs = float(eb)
         a = 1.0 if not alpha_override or alpha_override <= 0 else alpha_override
-    e, twoe, inv2e = level_bounds(eb_abs, a)
+    e, twoe, inv2e = level_bounds(eb_abs, a, levels(ndim))
     return eb_abs, e, twoe, inv2e
 
 
@@ -182,7 +198,7 @@ def compress(x: np.ndarray, cfg: Config, e, twoe, inv2e, eb_abs: float = float("
     dims = tuple(int(d) for d in x.shape)
     n = x.size
     cap = n if capacity is None else int(capacity)
-    anchors = np.zeros(anchor_count(dims), np.float32)
+    anchors = np.zeros(anchor_count(dims, cfg.ndim), np.float32)
     codes = np.zeros(n, np.uint16)
     out_idx = np.zeros(max(cap, 1), np.uint32)
     out_val = np.zeros(max(cap, 1), np.float32)
@@ -190,9 +206,11 @@ def compress(x: np.ndarray, cfg: Config, e, twoe, inv2e, eb_abs: float = float("
     e = np.ascontiguousarray(e, np.float32)
     twoe = np.ascontiguousarray(twoe, np.float32)
     inv2e = np.ascontiguousarray(inv2e, np.float32)
+    if min(e.size, twoe.size, inv2e.size) < levels(cfg.ndim):
+        raise ValueError(f"{levels(cfg.ndim)} level bounds needed")
     cnt = _load().orc_compress(_ptr(x), *dims, _ptr(_i32(cfg.order)), _ptr(_i32(cfg.level_kind)),
-                               _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x), int(cfg.radius), _ptr(e), _ptr(twoe),
-                               _ptr(inv2e),
+                               _ptr(_i32(cfg.cubic_kind)), int(cfg.domain_x), int(cfg.ndim), int(cfg.radius), _ptr(e),
+                               _ptr(twoe), _ptr(inv2e),
                                _ptr(anchors), _ptr(codes), _ptr(out_idx), _ptr(out_val), cap, _ptr(xr))
     if cnt < 0:
         raise RuntimeError(f"oracle compress failed ({cnt})")
@@ -208,7 +226,8 @@ def decompress(c: Compressed) -> np.ndarray:
     idx = np.ascontiguousarray(c.out_idx, np.uint32)
     val = np.ascontiguousarray(c.out_val, np.float32)
     rc = _load().orc_decompress(*c.dims, _ptr(_i32(c.cfg.order)), _ptr(_i32(c.cfg.level_kind)),
-                                _ptr(_i32(c.cfg.cubic_kind)), int(c.cfg.domain_x), int(c.cfg.radius), _ptr(c.twoe),
+                                _ptr(_i32(c.cfg.cubic_kind)), int(c.cfg.domain_x), int(c.cfg.ndim), int(c.cfg.radius),
+                                _ptr(np.ascontiguousarray(c.twoe, np.float32)),
                                 _ptr(np.ascontiguousarray(c.anchors, np.float32)), _ptr(codes), _ptr(idx), _ptr(val),
                                 int(idx.size), _ptr(xr))
     if rc != 0:
@@ -223,24 +242,24 @@ def histogram(codes: np.ndarray, radius: int) -> np.ndarray:
     return hist
 
 
-def profile(x: np.ndarray) -> np.ndarray:
+def profile(x: np.ndarray, ndim: int = 3) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float32)
     prof = np.zeros(PROFILE_LEN, np.float64)
-    _load().orc_profile(_ptr(x), *[int(d) for d in x.shape], _ptr(prof))
+    _load().orc_profile(_ptr(x), *[int(d) for d in x.shape], int(ndim), _ptr(prof))
     return prof
 
 
-def autotune_decide(prof: np.ndarray, radius: int = 512) -> Config:
+def autotune_decide(prof: np.ndarray, radius: int = 512, ndim: int = 3) -> Config:
     order = np.zeros(3, np.int32)
     lk = np.zeros(3, np.int32)
     ck = np.zeros(3, np.int32)
     _load().orc_autotune_decide(_ptr(np.ascontiguousarray(prof, np.float64)), _ptr(order), _ptr(lk), _ptr(ck))
-    return Config(tuple(int(v) for v in order), tuple(int(v) for v in lk), tuple(int(v) for v in ck), radius)
+    return Config(tuple(int(v) for v in order), tuple(int(v) for v in lk), tuple(int(v) for v in ck), radius,
+                  ndim=int(ndim))
 
 
-
-def autotune(x: np.ndarray, radius: int = 512) -> Config:
-    return autotune_decide(profile(x), radius)
+def autotune(x: np.ndarray, radius: int = 512, ndim: int = 3) -> Config:
+    return autotune_decide(profile(x, ndim), radius, ndim)
 
 
 def quality(hist: np.ndarray, radius: int, x: np.ndarray | None = None, xrec: np.ndarray | None = None) -> dict:

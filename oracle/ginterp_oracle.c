@@ -9,8 +9,16 @@
  * (no FMA contraction, IEEE float32/float64, default round-to-nearest-even).
  *
  * Notation (z, y, x), x fastest; i = (z*ny + y)*nx + x.  Axis ids 0=z, 1=y,
- * 2=x.  Level index l = 0, 1, 2 for strides s = 1, 2, 4 (the paper's level
- * ell = l + 1).  Per-level arrays (level_kind, e, twoe, inv2e) are indexed by l.
+ * 2=x.  Level index l = 0, 1, ... for strides s = 1, 2, 4, ... (the paper's
+ * level ell = l + 1).  Per-level arrays (e, twoe, inv2e) are indexed by l.
+ *
+ * Chunk geometry (Sec. IV-A): 8^3 chunks in 3-D, 16^2 in 2-D, 512 points in
+ * 1-D.  An ndim-D field is held as dims {nz, ny, nx}; its last ndim axes are
+ * chunked with anchor stride A = 8, 16 or 512 and interpolated at strides
+ * A/2, ..., 1 (3, 4 or 9 levels); the leading axes hold independent slices
+ * (2-D) or rows (1-D): every index along them is an anchor coordinate and
+ * nothing is interpolated along them.  level_kind has three entries; levels
+ * coarser than stride 4 follow level_kind[2].
  *
  * Readings of the paper taken here (each is also listed in the design doc):
  *   - neighbour domain is the closed 8^3 chunk [8*floor(n/8), min(.+8, n_d-1)]
@@ -44,18 +52,27 @@ double orc_alpha(double eps)
 
 /* ---- level-wise error bound e_ell = e / alpha^(ell-1) (Sec. IV-B.1) ----
  * Level l=0 is stride 1 (finest, the full bound); coarser levels get tighter
- * bounds.  alpha powers are formed by multiplication in double. */
-void orc_level_bounds(double eb_abs, double alpha, float e[3], float twoe[3], float inv2e[3])
+ * bounds.  alpha powers are formed by repeated multiplication in double. */
+void orc_level_bounds(double eb_abs, double alpha, int32_t nlev, float *e, float *twoe, float *inv2e)
 {
-    double apow[3];
-    apow[0] = 1.0;
-    apow[1] = alpha;
-    apow[2] = alpha * alpha;
-    for (int l = 0; l < 3; ++l) {
-        e[l] = (float)(eb_abs / apow[l]);
+    double apow = 1.0;
+    for (int l = 0; l < nlev; ++l) {
+        e[l] = (float)(eb_abs / apow);
         twoe[l] = 2.0f * e[l];
         inv2e[l] = (float)(1.0 / (2.0 * (double)e[l]));
+        apow *= alpha;
     }
+}
+
+/* ---- chunk geometry (Sec. IV-A) ---- */
+static int64_t chunk_edge(int ndim) { return ndim == 1 ? 512 : ndim == 2 ? 16 : 8; }
+
+int32_t orc_levels(int32_t ndim) { return ndim == 1 ? 9 : ndim == 2 ? 4 : 3; }
+
+/* anchor stride per axis: the chunk edge on the last ndim axes, 1 before them */
+static void anchor_strides(int ndim, int64_t A[3])
+{
+    for (int a = 0; a < 3; ++a) A[a] = (a >= 3 - ndim) ? chunk_edge(ndim) : 1;
 }
 
 /* ---- value range over finite values (Sec. IV-B.1, data profiling) ----
@@ -83,12 +100,15 @@ double orc_rel_to_abs(double eps, float vmin, float vmax)
     return eps * ((double)vmax - (double)vmin);
 }
 
-/* ---- anchor grid (Sec. IV-A): points whose coordinates are all multiples of 8 ---- */
-static int64_t anchors_along(int64_t n) { return (n - 1) / 8 + 1; }
+/* ---- anchor grid (Sec. IV-A): points whose chunked coordinates are all
+ * multiples of the chunk edge ---- */
+static int64_t anchors_along(int64_t n, int64_t a) { return (n - 1) / a + 1; }
 
-int64_t orc_anchor_count(int64_t nz, int64_t ny, int64_t nx)
+int64_t orc_anchor_count(int64_t nz, int64_t ny, int64_t nx, int32_t ndim)
 {
-    return anchors_along(nz) * anchors_along(ny) * anchors_along(nx);
+    int64_t A[3];
+    anchor_strides(ndim, A);
+    return anchors_along(nz, A[0]) * anchors_along(ny, A[1]) * anchors_along(nx, A[2]);
 }
 
 /* ---- 1-D splines (Sec. IV-B.1).  m3, m1, p1, p3 are x_{n-3s}, x_{n-s},
@@ -107,26 +127,32 @@ float orc_spline(int kind, float m3, float m1, float p1, float p3)
     }
 }
 
-/* ---- pass membership (Sec. IV-A): a non-anchor point belongs to level s =
- * largest power of two <= 4 dividing all coordinates, and, within the level,
- * to the pass of the LAST axis in dim order whose coordinate is an odd
- * multiple of s.  Returns the pass id 3*(2-l)+k (0..8, coarse first), or -1
- * for an anchor. ---- */
-static int pass_of(const int64_t c[3], const int order[3], int *axis, int *level)
+/* ---- pass membership (Sec. IV-A): a non-anchor point belongs to level l,
+ * the largest l < L with every chunked coordinate a multiple of s = 2^l, and,
+ * within the level, to the pass of the LAST chunked axis in dim order whose
+ * coordinate is an odd multiple of s.  Returns the pass id 3*(L-1-l)+k (coarse
+ * first), or -1 for an anchor. ---- */
+static int pass_of(const int64_t c[3], const int order[3], const int64_t A[3], int L, int *axis, int *level)
 {
-    int64_t all = c[0] | c[1] | c[2];
-    int l;
-    if ((all & 7) == 0) return -1;
-    if ((all & 3) == 0) l = 2;        /* stride 4 */
-    else if ((all & 1) == 0) l = 1;   /* stride 2 */
-    else l = 0;                       /* stride 1 */
+    int anchor = 1;
+    for (int a = 0; a < 3; ++a)
+        if (A[a] > 1 && c[a] % A[a] != 0) anchor = 0;
+    if (anchor) return -1;
+    int l = L - 1;
+    for (; l > 0; --l) {
+        int64_t s = (int64_t)1 << l;
+        int all = 1;
+        for (int a = 0; a < 3; ++a)
+            if (A[a] > 1 && c[a] % s != 0) all = 0;
+        if (all) break;
+    }
     int64_t s = (int64_t)1 << l;
     for (int k = 2; k >= 0; --k) {
         int a = order[k];
-        if (c[a] % (2 * s) == s) {
+        if (A[a] > 1 && c[a] % (2 * s) == s) {
             *axis = a;
             *level = l;
-            return 3 * (2 - l) + k;
+            return 3 * (L - 1 - l) + k;
         }
     }
     return -2; /* unreachable for a non-anchor point */
@@ -152,51 +178,61 @@ static int stencil_kind(int64_t n, int64_t s, int64_t nd, int spline, int cubic_
     return K_LINEAR;
 }
 
-/* Per-point schedule: pass id (255 for anchors) and stencil kind. */
-void orc_schedule_maps(int64_t nz, int64_t ny, int64_t nx, const int32_t order_in[3],
-                       const int32_t level_kind[3], const int32_t cubic_kind[3], int32_t domain_x,
-                       uint8_t *pass_map, uint8_t *kind_map)
+/* Shared traversal state of compress / decompress / debug prediction. */
+typedef struct {
+    int64_t dims[3];
+    int64_t A[3];     /* anchor stride per axis (1: not chunked, not interpolated) */
+    int64_t dom[3];   /* neighbour domain along each axis: the chunk edge, or 32 along x */
+    int L;            /* levels: strides 2^(L-1) .. 1 */
+    int order[3];
+    int level_kind[3];
+    int cubic_kind[3];
+} sched_t;
+
+static int sched_init(sched_t *S, int64_t nz, int64_t ny, int64_t nx, const int32_t order[3],
+                      const int32_t level_kind[3], const int32_t cubic_kind[3], int32_t domain_x, int32_t ndim)
 {
-    int order[3] = {order_in[0], order_in[1], order_in[2]};
-    int64_t dims[3] = {nz, ny, nx};
-    int64_t dom[3] = {8, 8, domain_x == 32 ? 32 : 8};
+    if (ndim < 1 || ndim > 3) return -1;
+    if (domain_x == 32 && ndim != 3) return -1;
+    S->dims[0] = nz; S->dims[1] = ny; S->dims[2] = nx;
+    anchor_strides(ndim, S->A);
+    for (int a = 0; a < 3; ++a) S->dom[a] = S->A[a];
+    if (domain_x == 32) S->dom[2] = 32;
+    S->L = orc_levels(ndim);
+    for (int a = 0; a < 3; ++a) {
+        S->order[a] = order[a];
+        S->level_kind[a] = level_kind[a];
+        S->cubic_kind[a] = cubic_kind[a];
+    }
+    return 0;
+}
+
+static int level_kind_of(const sched_t *S, int l) { return S->level_kind[l < 2 ? l : 2]; }
+
+/* Per-point schedule: pass id (255 for anchors) and stencil kind. */
+int orc_schedule_maps(int64_t nz, int64_t ny, int64_t nx, const int32_t order[3],
+                      const int32_t level_kind[3], const int32_t cubic_kind[3], int32_t domain_x, int32_t ndim,
+                      uint8_t *pass_map, uint8_t *kind_map)
+{
+    sched_t S;
+    if (sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x, ndim)) return -1;
     for (int64_t z = 0; z < nz; ++z)
         for (int64_t y = 0; y < ny; ++y)
             for (int64_t x = 0; x < nx; ++x) {
                 int64_t i = (z * ny + y) * nx + x;
                 int64_t c[3] = {z, y, x};
                 int axis = 0, level = 0;
-                int p = pass_of(c, order, &axis, &level);
+                int p = pass_of(c, S.order, S.A, S.L, &axis, &level);
                 if (p < 0) {
                     pass_map[i] = 255;
                     kind_map[i] = K_ANCHOR;
                     continue;
                 }
                 pass_map[i] = (uint8_t)p;
-                kind_map[i] = (uint8_t)stencil_kind(c[axis], (int64_t)1 << level, dims[axis],
-                                                    level_kind[level], cubic_kind[axis], dom[axis]);
+                kind_map[i] = (uint8_t)stencil_kind(c[axis], (int64_t)1 << level, S.dims[axis],
+                                                    level_kind_of(&S, level), S.cubic_kind[axis], S.dom[axis]);
             }
-}
-
-/* Shared traversal state of compress / decompress / debug prediction. */
-typedef struct {
-    int64_t dims[3];
-    int64_t dom[3];   /* neighbour domain along each axis: 8, or 32 along x */
-    int order[3];
-    int level_kind[3];
-    int cubic_kind[3];
-} sched_t;
-
-static void sched_init(sched_t *S, int64_t nz, int64_t ny, int64_t nx, const int32_t order[3],
-                       const int32_t level_kind[3], const int32_t cubic_kind[3], int32_t domain_x)
-{
-    S->dims[0] = nz; S->dims[1] = ny; S->dims[2] = nx;
-    S->dom[0] = 8; S->dom[1] = 8; S->dom[2] = domain_x == 32 ? 32 : 8;
-    for (int a = 0; a < 3; ++a) {
-        S->order[a] = order[a];
-        S->level_kind[a] = level_kind[a];
-        S->cubic_kind[a] = cubic_kind[a];
-    }
+    return 0;
 }
 
 /* Prediction of point c (level l, axis d) from array v (reconstructed values,
@@ -208,7 +244,7 @@ static float predict_point(const sched_t *S, const float *v, const uint8_t *know
     int64_t s = (int64_t)1 << l;
     int64_t stride_d = (d == 2) ? 1 : (d == 1) ? S->dims[2] : S->dims[1] * S->dims[2];
     int64_t i = (c[0] * S->dims[1] + c[1]) * S->dims[2] + c[2];
-    int kind = stencil_kind(c[d], s, S->dims[d], S->level_kind[l], S->cubic_kind[d], S->dom[d]);
+    int kind = stencil_kind(c[d], s, S->dims[d], level_kind_of(S, l), S->cubic_kind[d], S->dom[d]);
     float m3 = 0.0f, m1, p1 = 0.0f, p3 = 0.0f;
     int64_t im1 = i - s * stride_d, ip1 = i + s * stride_d;
     int64_t im3 = i - 3 * s * stride_d, ip3 = i + 3 * s * stride_d;
@@ -231,8 +267,8 @@ static float predict_point(const sched_t *S, const float *v, const uint8_t *know
 }
 
 /* Visit the points of pass (l, k) in ascending linear index: coordinate along
- * d = order[k] is an odd multiple of s, axes before d in the order are on the
- * s-grid, axes after d on the 2s-grid. */
+ * d = order[k] is an odd multiple of s, chunked axes before d in the order are on
+ * the s-grid, those after d on the 2s-grid; unchunked axes take every index. */
 typedef void (*visit_fn)(void *ctx, const int64_t c[3], int d, int l);
 
 static void for_each_in_pass(const sched_t *S, int l, int k, visit_fn fn, void *ctx)
@@ -242,7 +278,8 @@ static void for_each_in_pass(const sched_t *S, int l, int k, visit_fn fn, void *
     int64_t start[3], step[3];
     for (int j = 0; j < 3; ++j) {
         int a = S->order[j];
-        if (j == k) { start[a] = s; step[a] = 2 * s; }
+        if (S->A[a] == 1) { start[a] = 0; step[a] = 1; }
+        else if (j == k) { start[a] = s; step[a] = 2 * s; }
         else if (j < k) { start[a] = 0; step[a] = s; }
         else { start[a] = 0; step[a] = 2 * s; }
     }
@@ -255,9 +292,9 @@ static void for_each_in_pass(const sched_t *S, int l, int k, visit_fn fn, void *
 
 static void for_each_pass(const sched_t *S, visit_fn fn, void *ctx)
 {
-    for (int l = 2; l >= 0; --l)          /* strides 4, 2, 1 */
-        for (int k = 0; k < 3; ++k)       /* axes in dim order */
-            for_each_in_pass(S, l, k, fn, ctx);
+    for (int l = S->L - 1; l >= 0; --l)   /* strides 2^(L-1), ..., 2, 1 */
+        for (int k = 0; k < 3; ++k)       /* chunked axes in dim order */
+            if (S->A[S->order[k]] > 1) for_each_in_pass(S, l, k, fn, ctx);
 }
 
 static int64_t lin(const sched_t *S, const int64_t c[3])
@@ -329,13 +366,14 @@ static void collect_outliers(cctx_t *C, int64_t n)
 static void fill_anchors(const sched_t *S, const float *x, float *anchors, float *xr, uint8_t *known,
                          uint16_t *codes, int radius)
 {
-    int64_t ay = anchors_along(S->dims[1]), ax = anchors_along(S->dims[2]);
-    for (int64_t z = 0; z < S->dims[0]; z += 8)
-        for (int64_t y = 0; y < S->dims[1]; y += 8)
-            for (int64_t xx = 0; xx < S->dims[2]; xx += 8) {
+    const int64_t *A = S->A;
+    int64_t ay = anchors_along(S->dims[1], A[1]), ax = anchors_along(S->dims[2], A[2]);
+    for (int64_t z = 0; z < S->dims[0]; z += A[0])
+        for (int64_t y = 0; y < S->dims[1]; y += A[1])
+            for (int64_t xx = 0; xx < S->dims[2]; xx += A[2]) {
                 int64_t c[3] = {z, y, xx};
                 int64_t i = lin(S, c);
-                int64_t a = ((z / 8) * ay + y / 8) * ax + xx / 8;
+                int64_t a = ((z / A[0]) * ay + y / A[1]) * ax + xx / A[2];
                 if (x) anchors[a] = x[i];
                 xr[i] = anchors[a];
                 if (known) known[i] = 1;
@@ -348,12 +386,12 @@ static void fill_anchors(const sched_t *S, const float *x, float *anchors, float
  * schedule; cannot happen for a correct one).  xr receives x'. */
 int64_t orc_compress(const float *x, int64_t nz, int64_t ny, int64_t nx,
                      const int32_t order[3], const int32_t level_kind[3], const int32_t cubic_kind[3],
-                     int32_t domain_x, int32_t radius, const float e[3], const float twoe[3], const float inv2e[3],
-                     float *anchors, uint16_t *codes, uint32_t *out_idx, float *out_val,
+                     int32_t domain_x, int32_t ndim, int32_t radius, const float *e, const float *twoe,
+                     const float *inv2e, float *anchors, uint16_t *codes, uint32_t *out_idx, float *out_val,
                      int64_t capacity, float *xr)
 {
     sched_t S;
-    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x);
+    if (sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x, ndim)) return -2;
     int64_t n = nz * ny * nx;
     uint8_t *known = (uint8_t *)calloc((size_t)n, 1);
     if (!known) return -3;
@@ -400,12 +438,12 @@ static void decompress_visit(void *vctx, const int64_t c[3], int d, int l)
  * undefined read / missing outlier value. */
 int orc_decompress(int64_t nz, int64_t ny, int64_t nx,
                    const int32_t order[3], const int32_t level_kind[3], const int32_t cubic_kind[3],
-                   int32_t domain_x, int32_t radius, const float twoe[3],
+                   int32_t domain_x, int32_t ndim, int32_t radius, const float *twoe,
                    const float *anchors, const uint16_t *codes,
                    const uint32_t *out_idx, const float *out_val, int64_t n_out, float *xr)
 {
     sched_t S;
-    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x);
+    if (sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x, ndim)) return -2;
     int64_t n = nz * ny * nx;
     uint8_t *known = (uint8_t *)calloc((size_t)n, 1);
     if (!known) return -3;
@@ -444,12 +482,12 @@ static void predict_visit(void *vctx, const int64_t c[3], int d, int l)
     if (P->kind) P->kind[i] = (uint8_t)kind;
 }
 
-void orc_predict_original(const float *x, int64_t nz, int64_t ny, int64_t nx,
-                          const int32_t order[3], const int32_t level_kind[3],
-                          const int32_t cubic_kind[3], int32_t domain_x, float *pred, uint8_t *kind)
+int orc_predict_original(const float *x, int64_t nz, int64_t ny, int64_t nx,
+                         const int32_t order[3], const int32_t level_kind[3],
+                         const int32_t cubic_kind[3], int32_t domain_x, int32_t ndim, float *pred, uint8_t *kind)
 {
     sched_t S;
-    sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x);
+    if (sched_init(&S, nz, ny, nx, order, level_kind, cubic_kind, domain_x, ndim)) return -2;
     int64_t n = nz * ny * nx;
     for (int64_t i = 0; i < n; ++i) {
         pred[i] = x[i];
@@ -457,6 +495,7 @@ void orc_predict_original(const float *x, int64_t nz, int64_t ny, int64_t nx,
     }
     pctx_t P = {&S, x, pred, kind, 0};
     for_each_pass(&S, predict_visit, &P);
+    return 0;
 }
 
 /* ---------------- quant-code histogram (Fig. 1 statistics, Sec. V-A) ---------------- */
@@ -478,8 +517,9 @@ void orc_histogram(const uint16_t *codes, int64_t n, int32_t radius, uint32_t *h
  *   prof[12 + d]   += 2 |x - linear (stride 2)|
  *   prof[15 + d]   += |x - quad-left (stride 2)| + |x - quad-right (stride 2)|
  * (prof[3*d + 2] is unused).  A test whose neighbours fall outside the field
- * is skipped.  Sums are in double, in sample order (z, y, x ascending), axis
- * by axis. */
+ * is skipped, and so are the axes that are not chunked (the leading axes of a
+ * 1-D or 2-D field).  Sums are in double, in sample order (z, y, x ascending),
+ * axis by axis. */
 #define ORC_PROF_LEN 18
 
 static int64_t sample_coord(int64_t n, int j)
@@ -489,12 +529,12 @@ static int64_t sample_coord(int64_t n, int j)
     return lo + (int64_t)j * (n - 1 - 2 * lo) / 3;
 }
 
-void orc_profile(const float *x, int64_t nz, int64_t ny, int64_t nx, double *prof)
+void orc_profile(const float *x, int64_t nz, int64_t ny, int64_t nx, int32_t ndim, double *prof)
 {
     int64_t dims[3] = {nz, ny, nx};
     int64_t stride[3] = {ny * nx, nx, 1};
     for (int t = 0; t < ORC_PROF_LEN; ++t) prof[t] = 0.0;
-    for (int d = 0; d < 3; ++d)
+    for (int d = 3 - ndim; d < 3; ++d)
         for (int jz = 0; jz < 4; ++jz)
             for (int jy = 0; jy < 4; ++jy)
                 for (int jx = 0; jx < 4; ++jx) {

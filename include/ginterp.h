@@ -24,8 +24,10 @@
  *     errors (detected on the host before anything is enqueued) and launch
  *     errors.  Conditions found on the device are reported in
  *     interp_header.status (bit flags INTERP_STATUS_*).
- *   - Level index l = 0, 1, 2 refers to strides 1, 2, 4 (the paper's level
- *     ell = l + 1); per-level arrays are indexed by l.
+ *   - Level index l = 0, 1, 2, ... refers to strides 1, 2, 4, ... (the paper's
+ *     level ell = l + 1); per-level arrays are indexed by l.  The header keeps
+ *     the bounds of l = 0..2; the 1-D and 2-D geometries (cfg.ndim) continue
+ *     e_l = e / alpha^l to their 9 and 4 levels.
  */
 #ifndef GINTERP_H
 #define GINTERP_H
@@ -72,6 +74,13 @@ typedef struct {
                               (Sec. IV-A, Fig. 3); 32 = the closed 32-point block of the
                               32x8x8 data blocks, whose four chunks share points along x
                               (Sec. IV-C).  Anchors stay on the stride-8 grid either way. */
+    int32_t ndim;          /* chunk geometry (Sec. IV-A): 0 or 3 = 8^3 chunks, strides 4, 2, 1;
+                              2 = 16^2 chunks over (y, x), strides 8 .. 1, every z-slice on its
+                              own; 1 = 512-point chunks along x, strides 256 .. 1, every (z, y)
+                              row on its own.  Levels coarser than stride 4 use level_kind[2];
+                              their bounds continue e_l = e / alpha^l.  1 and 2 need domain_x
+                              0 or 8 and are taken by interp_compress / interp_decompress_nd
+                              only (not by the batched or no-allocation forms). */
     double alpha;          /* error-bound reduction factor; <= 0 selects Eq. 1 A(eps) in
                               relative mode and 1 in absolute mode */
 } interp_config;
@@ -97,6 +106,11 @@ typedef struct {
 /* Number of anchor points: prod over axes of (floor((n_d - 1) / 8) + 1) (Sec. IV-A).
  * Returns 0 for invalid dims. */
 size_t interp_anchor_count(const int64_t dims[3]);
+
+/* Anchor count of the ndim-D geometry (cfg.ndim): prod over axes of
+ * (floor((n_d - 1) / A_d) + 1) with A_d the chunk edge (8, 16 or 512) on the last
+ * ndim axes and 1 on the others.  0 for invalid dims or ndim. */
+size_t interp_anchor_count_nd(const int64_t dims[3], int32_t ndim);
 
 /* Device scratch that interp_compress needs, in bytes (0 for invalid args). */
 size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg);
@@ -135,6 +149,12 @@ int interp_compress(const float *d_x, const int64_t dims[3], double eb, const in
 int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const float *d_anchors,
                       const uint16_t *d_codes, const uint32_t *d_out_idx, const float *d_out_val,
                       uint64_t out_capacity, float *d_xrec, interp_stream_t stream);
+
+/* interp_decompress for a field compressed with cfg.ndim = ndim (1, 2 or 3; 3 is
+ * interp_decompress itself).  Same arguments and results. */
+int interp_decompress_nd(int32_t ndim, const int64_t dims[3], const interp_header *d_hdr,
+                         const float *d_anchors, const uint16_t *d_codes, const uint32_t *d_out_idx,
+                         const float *d_out_val, uint64_t out_capacity, float *d_xrec, interp_stream_t stream);
 
 /* Batched forms: n fields of any (uneven) shapes, bounds and configurations in one call.
  * Each item carries exactly the arguments of the single-field call (its own workspace).
@@ -195,7 +215,8 @@ int interp_value_range(const float *d_x, const int64_t dims[3], float *d_range, 
 
 /* Sampling profile and decision (Sec. IV-B.1 data profiling, Sec. IV-B.2 auto-tuning):
  * fills h_cfg->dim_order, cubic_kind and level_kind from the 4x4x4 sample profile of
- * d_x and writes the 18 profile sums to h_profile (may be NULL).  Uses 512 bytes of
+ * d_x (along the chunked axes of h_cfg->ndim only; the other axes' sums are 0 and they
+ * sort last) and writes the 18 profile sums to h_profile (may be NULL).  Uses 512 bytes of
  * d_ws.  SYNCHRONISES the stream (one small device-to-host copy). */
 int interp_autotune(const float *d_x, const int64_t dims[3], interp_config *h_cfg,
                     double *h_profile, void *d_ws, size_t ws_bytes, interp_stream_t stream);

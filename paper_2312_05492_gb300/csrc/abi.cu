@@ -43,6 +43,10 @@ bool cfg_ok(const interp_config *c)
     if (seen != 7) return false;
     if (c->eb_mode != 0 && c->eb_mode != 1) return false;
     if (c->domain_x != 0 && c->domain_x != 8 && c->domain_x != 32) return false;
+    if (c->ndim < 0 || c->ndim > 3) return false;
+    if (c->ndim == 1 || c->ndim == 2) {
+        if (c->domain_x == 32) return false;
+    }
     if (c->autotune != 0 && c->autotune != 1) return false;
     if (c->radius < 2 || c->radius > 32768) return false;
     if (std::isnan(c->alpha) || std::isinf(c->alpha)) return false;
@@ -136,10 +140,62 @@ size_t interp_anchor_count(const int64_t dims[3])
     return n;
 }
 
+size_t interp_anchor_count_nd(const int64_t dims[3], int32_t ndim)
+{
+    if (!dims_ok(dims) || ndim < 0 || ndim > 3) return 0;
+    if (ndim == 0 || ndim == 3) return interp_anchor_count(dims);
+    const int64_t edge = ndim == 2 ? 16 : 512;
+    size_t n = 1;
+    for (int a = 0; a < 3; ++a) n *= (size_t)((dims[a] - 1) / (a >= 3 - ndim ? edge : 1) + 1);
+    return n;
+}
+
 size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg)
 {
     if (!dims_ok(dims) || !cfg_ok(cfg)) return 0;
     return ws_layout(dims).total;
+}
+
+// One field in the 1-D or 2-D geometry: the same setup and compaction as the 3-D
+// path around the per-tile kernel of nd.cu.
+int compress_nd(const interp_compress_item &it, interp_stream_t stream)
+{
+    const interp_config &c = it.cfg;
+    if (!dims_ok(it.dims) || !cfg_ok(&c)) return INTERP_EINVAL;
+    if (!(it.eb > 0.0) || std::isinf(it.eb)) return INTERP_EINVAL;
+    if (!it.d_x || !it.d_anchors || !it.d_codes || !it.d_hdr || !it.d_ws) return INTERP_EINVAL;
+    if (it.out_capacity > 0 && (!it.d_out_idx || !it.d_out_val)) return INTERP_EINVAL;
+    const WsLayout L = ws_layout(it.dims);
+    if (it.ws_bytes < L.total) return INTERP_EWORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Dims d = to_dims(it.dims);
+    const double alpha = effective_alpha(c, it.eb);
+    unsigned char *ws = static_cast<unsigned char *>(it.d_ws);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(ws + L.ctrl);
+    uint32_t *bitmap = reinterpret_cast<uint32_t *>(ws + L.bitmap);
+    uint32_t *blockcnt = reinterpret_cast<uint32_t *>(ws + L.blockcnt);
+    cudaError_t e = cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(blockcnt, 0, sizeof(uint32_t) * (size_t)L.nblk, s);
+    if (e == cudaSuccess && it.d_hist) e = cudaMemsetAsync(it.d_hist, 0, sizeof(uint32_t) * 2 * (size_t)c.radius, s);
+    if (e == cudaSuccess && c.autotune) e = gi::launch_profile(it.d_x, d, it.d_hdr, 1, s, c.ndim);
+    if (e == cudaSuccess) {
+        if (c.eb_mode)
+            e = gi::launch_range(it.d_x, d, it.eb, c, alpha, it.d_hdr, ws + L.partials, counter, gi::range_blocks(),
+                                 s);
+        else
+            e = gi::launch_header_init(it.d_hdr, d, it.eb, c, alpha, s);
+    }
+    const gi::CompressArgs args{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
+                                it.d_hdr, false, false, 1};
+    if (e == cudaSuccess) {
+        timing_mark(0, 0, s);
+        e = gi::launch_nd_compress(c.ndim, args, s);
+        timing_mark(0, 1, s);
+    }
+    if (e == cudaSuccess)
+        e = gi::launch_outlier_compaction(bitmap, blockcnt, L.words, d, it.d_x, it.d_out_idx, it.d_out_val,
+                                          it.out_capacity, it.d_hdr, s);
+    return cuda_status(e);
 }
 
 int interp_compress_batched(const interp_compress_item *items, int n, interp_stream_t stream)
@@ -149,6 +205,7 @@ int interp_compress_batched(const interp_compress_item *items, int n, interp_str
     for (int i = 0; i < n; ++i) {  // every argument is checked before anything is enqueued
         const interp_compress_item &it = items[i];
         if (!dims_ok(it.dims) || !cfg_ok(&it.cfg)) return INTERP_EINVAL;
+        if (it.cfg.ndim == 1 || it.cfg.ndim == 2) return INTERP_EINVAL;  // single-field calls only
         if (!(it.eb > 0.0) || std::isinf(it.eb)) return INTERP_EINVAL;
         if (!it.d_x || !it.d_anchors || !it.d_codes || !it.d_hdr || !it.d_ws) return INTERP_EINVAL;
         if (it.out_capacity > 0 && (!it.d_out_idx || !it.d_out_val)) return INTERP_EINVAL;
@@ -215,6 +272,7 @@ int interp_compress(const float *d_x, const int64_t dims[3], double eb, const in
     it.d_hdr = d_hdr;
     it.d_ws = d_ws;
     it.ws_bytes = ws_bytes;
+    if (cfg->ndim == 1 || cfg->ndim == 2) return compress_nd(it, stream);
     return interp_compress_batched(&it, 1, stream);
 }
 
@@ -261,6 +319,30 @@ int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const f
     it.out_capacity = out_capacity;
     it.d_xrec = d_xrec;
     return interp_decompress_batched(&it, 1, stream);
+}
+
+int interp_decompress_nd(int32_t ndim, const int64_t dims[3], const interp_header *d_hdr,
+                         const float *d_anchors, const uint16_t *d_codes, const uint32_t *d_out_idx,
+                         const float *d_out_val, uint64_t out_capacity, float *d_xrec, interp_stream_t stream)
+{
+    if (ndim == 0 || ndim == 3)
+        return interp_decompress(dims, d_hdr, d_anchors, d_codes, d_out_idx, d_out_val, out_capacity, d_xrec,
+                                 stream);
+    if (ndim != 1 && ndim != 2) return INTERP_EINVAL;
+    if (!dims_ok(dims)) return INTERP_EINVAL;
+    if (!d_hdr || !d_anchors || !d_codes || !d_xrec) return INTERP_EINVAL;
+    if (out_capacity > 0 && (!d_out_idx || !d_out_val)) return INTERP_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Dims d = to_dims(dims);
+    cudaError_t e = cudaSuccess;
+    if (out_capacity > 0) e = gi::launch_outlier_scatter(d_hdr, d_out_idx, d_out_val, out_capacity, d_xrec, s);
+    const gi::DecompressArgs args{d, d_anchors, d_codes, d_xrec, d_hdr, false};
+    if (e == cudaSuccess) {
+        timing_mark(1, 0, s);
+        e = gi::launch_nd_decompress(ndim, args, s);
+        timing_mark(1, 1, s);
+    }
+    return cuda_status(e);
 }
 
 int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_t *d_hist, interp_stream_t stream)
@@ -361,7 +443,8 @@ int interp_autotune(const float *d_x, const int64_t dims[3], interp_config *h_cf
     if (ws_bytes < sizeof(interp_header)) return INTERP_EWORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     interp_header *tmp = static_cast<interp_header *>(d_ws);
-    cudaError_t e = gi::launch_profile(d_x, to_dims(dims), tmp, 1, s);
+    if (h_cfg->ndim < 0 || h_cfg->ndim > 3) return INTERP_EINVAL;
+    cudaError_t e = gi::launch_profile(d_x, to_dims(dims), tmp, 1, s, h_cfg->ndim);
     interp_header h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, tmp, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

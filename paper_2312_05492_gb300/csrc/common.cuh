@@ -147,9 +147,22 @@ struct DecompressArgs {
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Bitmap word gw (ascending index order: row = gw / words_per_row of the (z, y)
+// rows, 32 x-positions each) lives at a tile-major address: rows are grouped by
+// OY along y, and a group's words of one 32-column strip are contiguous per z.
+__device__ __forceinline__ size_t tiled_word(long long gw, int words_per_row, int ny, int nz)
+{
+    const long long row = gw / words_per_row;
+    const int cx = (int)(gw - row * words_per_row);
+    const int gz = (int)(row / ny), gy = (int)(row - (long long)gz * ny);
+    const size_t col = (size_t)(gy / OY) * words_per_row + cx;
+    return (col * nz + gz) * OY + (gy % OY);
+}
+
 cudaError_t launch_header_init(interp_header *hdr, Dims d, double eb, interp_config cfg, double alpha,
                                cudaStream_t s);
-cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s);
+cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s,
+                           int ndim = 3);
 cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, double alpha, interp_header *hdr,
                          void *partials, unsigned int *counter, int nblocks, cudaStream_t s,
                          float *out_range = nullptr);  // hdr == nullptr: write {vmin, vmax} to out_range
@@ -157,6 +170,9 @@ cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, d
 cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s);
 cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s);
 size_t bitmap_words_tiled(Dims d);
+// 1-D (512-point chunks) and 2-D (16^2 chunks) variants (nd.cu); ndim 1 or 2
+cudaError_t launch_nd_compress(int ndim, const CompressArgs &a, cudaStream_t s);
+cudaError_t launch_nd_decompress(int ndim, const DecompressArgs &a, cudaStream_t s);
 cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
                                       const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
                                       interp_header *hdr, cudaStream_t s);

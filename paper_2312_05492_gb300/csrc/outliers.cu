@@ -61,18 +61,6 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_outlier_scan(uint32_t *blockcn
     }
 }
 
-// Word gw (ascending index order: row = gw / words_per_row, 32 x-positions
-// each) lives at a tile-major address: the compression tiles own OY rows x 32
-// columns and write their words contiguously per plane.
-__device__ __forceinline__ size_t tiled_word(long long gw, int words_per_row, int ny, int nz)
-{
-    const long long row = gw / words_per_row;
-    const int cx = (int)(gw - row * words_per_row);
-    const int gz = (int)(row / ny), gy = (int)(row - (long long)gz * ny);
-    const size_t col = (size_t)(gy / OY) * words_per_row + cx;
-    return (col * nz + gz) * OY + (gy % OY);
-}
-
 __global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const uint32_t *__restrict__ bitmap,
                                                                  const uint32_t *__restrict__ offsets,
                                                                  long long words, int words_per_row, int nx, int ny,

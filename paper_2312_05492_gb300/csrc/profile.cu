@@ -38,6 +38,7 @@ __device__ void write_bounds(interp_header *h, Dims d, double eb, const interp_c
     h->cfg.autotune = cfg.autotune;
     h->cfg.radius = cfg.radius;
     h->cfg.domain_x = cfg.domain_x;
+    h->cfg.ndim = cfg.ndim;
     h->cfg.alpha = cfg.alpha;
     const double eb_abs = cfg.eb_mode ? eb * ((double)vmax - (double)vmin) : eb;
     h->eb = eb;
@@ -196,7 +197,7 @@ constexpr int PROFILE_SAMPLES = 64;
 //   2 |x - linear (stride 2)|, |x - quad-left (stride 2)| + |x - quad-right (stride 2)|.
 // Sums per (axis, term) in sample order (z, y, x ascending), in double.
 __global__ void __launch_bounds__(3 * PROFILE_SAMPLES) k_profile(const float *__restrict__ x, Dims d,
-                                                                interp_header *hdr, int apply)
+                                                                interp_header *hdr, int apply, int first_axis)
 {
     __shared__ double terms[3][5][PROFILE_SAMPLES];
     __shared__ double prof[18];
@@ -210,13 +211,14 @@ __global__ void __launch_bounds__(3 * PROFILE_SAMPLES) k_profile(const float *__
     const long long sd = st[axis];
     const double xv = (double)x[i];
     double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0;
-    if (n - 3 >= 0 && n + 3 <= nd - 1) {
+    const bool chunked = axis >= first_axis;  // the leading axes of 1-D / 2-D data are not profiled
+    if (chunked && n - 3 >= 0 && n + 3 <= nd - 1) {
         const float m3 = x[i - 3 * sd], m1 = x[i - sd], p1 = x[i + sd], p3 = x[i + 3 * sd];
         t0 = fabs(xv - (double)sp_cubic(cubic_coeffs(0), m3, m1, p1, p3));
         t1 = fabs(xv - (double)sp_cubic(cubic_coeffs(1), m3, m1, p1, p3));
     }
-    if (n - 1 >= 0 && n + 1 <= nd - 1) t2 = fabs(xv - (double)sp_linear(x[i - sd], x[i + sd]));
-    if (n - 6 >= 0 && n + 6 <= nd - 1) {
+    if (chunked && n - 1 >= 0 && n + 1 <= nd - 1) t2 = fabs(xv - (double)sp_linear(x[i - sd], x[i + sd]));
+    if (chunked && n - 6 >= 0 && n + 6 <= nd - 1) {
         const float m3 = x[i - 6 * sd], m1 = x[i - 2 * sd], p1 = x[i + 2 * sd], p3 = x[i + 6 * sd];
         t3 = 2.0 * fabs(xv - (double)sp_linear(m1, p1));
         t4 = fabs(xv - (double)sp_quad_left(m3, m1, p1)) + fabs(xv - (double)sp_quad_right(m1, p1, p3));
@@ -309,9 +311,10 @@ cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s)
+cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s, int ndim)
 {
-    k_profile<<<1, 3 * PROFILE_SAMPLES, 0, s>>>(x, d, hdr, apply_decision);
+    const int first_axis = (ndim == 1 || ndim == 2) ? 3 - ndim : 0;
+    k_profile<<<1, 3 * PROFILE_SAMPLES, 0, s>>>(x, d, hdr, apply_decision, first_axis);
     return cudaGetLastError();
 }
 

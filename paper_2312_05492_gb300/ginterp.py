@@ -28,7 +28,7 @@ FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress",
              "interp_decompress_batched", "interp_status_string", "interp_alpha", "interp_value_range",
              "interp_quality_workspace_bytes", "interp_quality_report", "interp_huffman_codebook",
              "interp_huffman_chunks", "interp_huffman_capacity_words", "interp_huffman_workspace_bytes",
-             "interp_huffman_encode", "interp_huffman_decode")
+             "interp_huffman_encode", "interp_huffman_decode", "interp_anchor_count_nd", "interp_decompress_nd")
 
 # kernels each call launches (memsets excluded): compress = [profile] + range or
 # header + tiles + outlier scan + outlier write; decompress = scatter + tiles
@@ -42,7 +42,8 @@ LAUNCHES_DECOMPRESS = 2
 class interp_config(ctypes.Structure):
     _fields_ = [("dim_order", ctypes.c_int32 * 3), ("level_kind", ctypes.c_int32 * 3),
                 ("cubic_kind", ctypes.c_int32 * 3), ("eb_mode", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("radius", ctypes.c_int32), ("domain_x", ctypes.c_int32), ("alpha", ctypes.c_double)]
+                ("radius", ctypes.c_int32), ("domain_x", ctypes.c_int32), ("ndim", ctypes.c_int32),
+                ("alpha", ctypes.c_double)]
 
 
 class interp_header(ctypes.Structure):
@@ -96,6 +97,10 @@ def load() -> ctypes.CDLL:
     cfg_p = ctypes.POINTER(interp_config)
     lib.interp_anchor_count.restype = ctypes.c_size_t
     lib.interp_anchor_count.argtypes = [dims_t]
+    lib.interp_anchor_count_nd.restype = ctypes.c_size_t
+    lib.interp_anchor_count_nd.argtypes = [dims_t, i32]
+    lib.interp_decompress_nd.restype = ctypes.c_int
+    lib.interp_decompress_nd.argtypes = [i32, dims_t, P, P, P, P, P, u64, P, P]
     lib.interp_workspace_bytes.restype = ctypes.c_size_t
     lib.interp_workspace_bytes.argtypes = [dims_t, cfg_p]
     lib.interp_compress.restype = ctypes.c_int
@@ -163,6 +168,16 @@ def _stream_ptr(stream) -> int:
 # ----------------------------------------------------------- C-name entry points
 def interp_anchor_count(dims) -> int:
     return int(load().interp_anchor_count(_dims(dims)))
+
+
+def interp_anchor_count_nd(dims, ndim: int) -> int:
+    return int(load().interp_anchor_count_nd(_dims(dims), int(ndim)))
+
+
+def interp_decompress_nd(ndim, dims, d_hdr, d_anchors, d_codes, d_out_idx, d_out_val, out_capacity, d_xrec,
+                         stream) -> int:
+    return load().interp_decompress_nd(int(ndim), _dims(dims), d_hdr, d_anchors, d_codes, d_out_idx, d_out_val,
+                                       int(out_capacity), d_xrec, stream)
 
 
 def interp_workspace_bytes(dims, cfg: interp_config) -> int:
@@ -251,6 +266,9 @@ class Config:
     level_kind is indexed by level l (stride 2**l): 0 = linear only, 1 = splines.
     cubic_kind is indexed by axis (0=z, 1=y, 2=x): 0 = not-a-knot, 1 = natural.
     domain_x: neighbour domain along x, 8 (the 8^3 chunk) or 32 (the x-extended block).
+    ndim: chunk geometry (Sec. IV-A): 3 = 8^3 chunks; 2 = 16^2 chunks over (y, x) of
+      every z-slice; 1 = 512-point chunks along x of every row.  Levels coarser than
+      stride 4 follow level_kind[2].
     """
     dim_order: tuple = (0, 1, 2)
     level_kind: tuple = (1, 1, 1)
@@ -260,6 +278,7 @@ class Config:
     radius: int = 512
     alpha: float = 0.0
     domain_x: int = 8
+    ndim: int = 3
 
     def to_c(self) -> interp_config:
         c = interp_config()
@@ -270,6 +289,7 @@ class Config:
         c.autotune = 1 if self.autotune else 0
         c.radius = int(self.radius)
         c.domain_x = int(self.domain_x)
+        c.ndim = int(self.ndim)
         c.alpha = float(self.alpha)
         return c
 
@@ -348,7 +368,7 @@ def allocate(dims, cfg: Config, device, capacity: int | None = None, hist: bool 
     cap = default_capacity(n) if capacity is None else int(capacity)
     return dict(
         header=torch.zeros(HEADER_BYTES, dtype=torch.uint8, device=device),
-        anchors=torch.empty(interp_anchor_count(dims), dtype=torch.float32, device=device),
+        anchors=torch.empty(interp_anchor_count_nd(dims, cfg.ndim), dtype=torch.float32, device=device),
         codes=torch.empty(n, dtype=torch.int16, device=device),
         out_idx=torch.empty(max(cap, 1), dtype=torch.int32, device=device),
         out_val=torch.empty(max(cap, 1), dtype=torch.float32, device=device),
@@ -367,8 +387,12 @@ def compress_into(x: torch.Tensor, eb: float, cfg: Config, bufs: dict, ws: torch
 
 
 def decompress_into(cf: CompressedField, out: torch.Tensor, stream=None) -> None:
-    rc = interp_decompress(cf.dims, _ptr(cf.header), _ptr(cf.anchors), _ptr(cf.codes), _ptr(cf.out_idx),
-                           _ptr(cf.out_val), cf.capacity, _ptr(out), _stream_ptr(stream))
+    if cf.cfg.ndim in (1, 2):
+        rc = interp_decompress_nd(cf.cfg.ndim, cf.dims, _ptr(cf.header), _ptr(cf.anchors), _ptr(cf.codes),
+                                  _ptr(cf.out_idx), _ptr(cf.out_val), cf.capacity, _ptr(out), _stream_ptr(stream))
+    else:
+        rc = interp_decompress(cf.dims, _ptr(cf.header), _ptr(cf.anchors), _ptr(cf.codes), _ptr(cf.out_idx),
+                               _ptr(cf.out_val), cf.capacity, _ptr(out), _stream_ptr(stream))
     _check(rc, "interp_decompress")
 
 
@@ -523,18 +547,19 @@ def huffman_decode(hs: HuffmanStream, out: torch.Tensor | None = None, stream=No
     return out
 
 
-def autotune(x: torch.Tensor, radius: int = 512, stream=None):
+def autotune(x: torch.Tensor, radius: int = 512, stream=None, ndim: int = 3):
     """Sampling profile + decision on the device; returns (Config, profile sums)."""
     _check_field(x)
     c = interp_config()
     c.radius = radius
+    c.ndim = int(ndim)
     prof = (ctypes.c_double * 18)()
     ws = torch.empty(HEADER_BYTES, dtype=torch.uint8, device=x.device)
     rc = interp_autotune(_ptr(x), tuple(x.shape), c, ctypes.addressof(prof), _ptr(ws), ws.numel(),
                          _stream_ptr(stream))
     _check(rc, "interp_autotune")
     cfg = Config(dim_order=tuple(c.dim_order), level_kind=tuple(c.level_kind), cubic_kind=tuple(c.cubic_kind),
-                 radius=radius)
+                 radius=radius, ndim=int(ndim))
     return cfg, [float(v) for v in prof]
 
 

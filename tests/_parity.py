@@ -26,7 +26,7 @@ def gpu_roundtrip(x_np: np.ndarray, eb: float, cfg: G.Config, capacity: int | No
 def oracle_cfg_from_header(h, radius: int) -> O.Config:
     return O.Config(order=tuple(h.cfg.dim_order), level_kind=tuple(h.cfg.level_kind),
                     cubic_kind=tuple(h.cfg.cubic_kind), radius=radius,
-                    domain_x=32 if h.cfg.domain_x == 32 else 8)
+                    domain_x=32 if h.cfg.domain_x == 32 else 8, ndim=h.cfg.ndim if h.cfg.ndim in (1, 2) else 3)
 
 
 def assert_parity(x_np: np.ndarray, eb: float, cfg: G.Config, capacity: int | None = None, check_hist=True):
@@ -35,22 +35,25 @@ def assert_parity(x_np: np.ndarray, eb: float, cfg: G.Config, capacity: int | No
     x_np = np.ascontiguousarray(x_np, np.float32)
     cf, xr, h = gpu_roundtrip(x_np, eb, cfg, capacity, hist=check_hist)
     mode = cfg.eb_mode
-    # bounds: range, alpha and level bounds identical to the oracle's
-    eb_abs, e, twoe, inv2e = O.bounds_for(x_np, eb, mode, cfg.alpha if cfg.alpha > 0 else None)
+    ndim = cfg.ndim if cfg.ndim in (1, 2) else 3
+    # bounds: range, alpha and level bounds identical to the oracle's (the header
+    # holds the first three levels; the 1-D / 2-D kernels continue the sequence)
+    eb_abs, e, twoe, inv2e = O.bounds_for(x_np, eb, mode, cfg.alpha if cfg.alpha > 0 else None, ndim=ndim)
     assert h.eb_abs == eb_abs, (h.eb_abs, eb_abs)
-    assert np.array_equal(bits(np.array(h.e[:], np.float32)), bits(e))
-    assert np.array_equal(bits(np.array(h.twoe[:], np.float32)), bits(twoe))
-    assert np.array_equal(bits(np.array(h.inv2e[:], np.float32)), bits(inv2e))
+    assert np.array_equal(bits(np.array(h.e[:], np.float32)), bits(e[:3]))
+    assert np.array_equal(bits(np.array(h.twoe[:], np.float32)), bits(twoe[:3]))
+    assert np.array_equal(bits(np.array(h.inv2e[:], np.float32)), bits(inv2e[:3]))
+    assert h.cfg.ndim == cfg.ndim
     # configuration: the oracle's own autotune decision when autotuning
     if cfg.autotune:
-        ocfg = O.autotune(x_np, cfg.radius)
+        ocfg = O.autotune(x_np, cfg.radius, ndim=ndim)
         ocfg.domain_x = 32 if cfg.domain_x == 32 else 8
-        prof = O.profile(x_np)
+        prof = O.profile(x_np, ndim)
         assert np.array_equal(np.array(h.profile[:], np.float64).view(np.uint64), prof.view(np.uint64))
     else:
         ocfg = O.Config(order=tuple(cfg.dim_order), level_kind=tuple(cfg.level_kind),
                         cubic_kind=tuple(cfg.cubic_kind), radius=cfg.radius,
-                        domain_x=32 if cfg.domain_x == 32 else 8)
+                        domain_x=32 if cfg.domain_x == 32 else 8, ndim=ndim)
     assert tuple(h.cfg.dim_order) == tuple(ocfg.order)
     assert tuple(h.cfg.level_kind) == tuple(ocfg.level_kind)
     assert tuple(h.cfg.cubic_kind) == tuple(ocfg.cubic_kind)
@@ -76,10 +79,11 @@ def assert_parity(x_np: np.ndarray, eb: float, cfg: G.Config, capacity: int | No
 
 def assert_bound(x_np, xr, cfg: O.Config, e):
     pm, _ = O.schedule_maps(x_np.shape, cfg)
-    lvl = np.where(pm == 255, -1, 2 - pm.astype(np.int64) // 3)
+    L = O.levels(cfg.ndim)
+    lvl = np.where(pm == 255, -1, L - 1 - pm.astype(np.int64) // 3)
     fin = np.isfinite(x_np)
     err = np.abs(xr.astype(np.float64) - x_np.astype(np.float64))
-    for l in range(3):
+    for l in range(L):
         m = (lvl == l) & fin
         assert np.all(err[m] <= e[l]), (l, float(err[m].max()), float(e[l]))
     assert np.all(bits(xr)[~fin] == bits(x_np)[~fin])

@@ -164,6 +164,59 @@ def quality_summary(G, cf, x, xrec) -> dict:
             "max_abs_err": q["max_abs_err"]}
 
 
+def nd_variant(G, ndim: int, eb: float, stream, peak: float) -> dict:
+    """The 2-D (16^2 chunks, 32 slices of 2048^2) or 1-D (512-point chunks, 64 rows of
+    2^21) geometry of Sec. IV-A on a field of the same 512 MiB: tile-kernel times
+    (library events, 10 launches each), their fraction of the HBM roofline, and the
+    bound check.  Outside the timed region."""
+    import torch
+
+    from paper_2312_05492_gb300 import fields
+    shape = (32, 2048, 2048) if ndim == 2 else (64, 1, 1 << 21)
+    x = fields.grf(shape, 3.0, 5, device="cuda", fft_dtype=torch.float32)
+    torch.cuda.empty_cache()
+    cfg = G.Config(autotune=True, ndim=ndim)
+    dims = tuple(shape)
+    bufs = G.allocate(dims, cfg, x.device, capacity=x.numel() // 16)
+    ws = torch.empty(G.interp_workspace_bytes(dims, cfg.to_c()), dtype=torch.uint8, device=x.device)
+    cf = G.CompressedField(dims, cfg, bufs["header"], bufs["anchors"], bufs["codes"], bufs["out_idx"],
+                           bufs["out_val"], bufs["hist"], bufs["capacity"])
+    xr = torch.empty_like(x)
+    for _ in range(2):
+        G.compress_into(x, eb, cfg, bufs, ws, stream)
+        G.decompress_into(cf, xr, stream)
+    torch.cuda.synchronize()
+    G.interp_timing_enable(True)
+    for _ in range(10):
+        G.compress_into(x, eb, cfg, bufs, ws, stream)
+        G.decompress_into(cf, xr, stream)
+    torch.cuda.synchronize()
+    G.interp_timing_enable(False)
+    cm, cn, dm, dn = G.interp_timing_read()
+    h = cf.host_header(refresh=True)
+    assert h.status == 0 and float((xr - x).abs().max()) <= level0_bound(h)
+    n = x.numel()
+    A = cf.anchors.numel()
+    # algorithmic bytes: field in, codes out, anchors out, outlier bitmap words
+    # (compression); codes and anchors in, field out (decompression)
+    c_alg = 4 * n + 2 * n + 4 * A + 4 * ((n + 31) // 32)
+    d_alg = 2 * n + 4 * A + 4 * n
+    c_ms, d_ms = cm / max(cn, 1), dm / max(dn, 1)
+    q = quality_summary(G, cf, x, xr)
+    out = {"ndim": ndim, "shape": list(shape), "chunk": "16^2" if ndim == 2 else "512",
+           "dim_order": list(h.cfg.dim_order), "compress_tile_ms": round(c_ms, 4),
+           "decompress_tile_ms": round(d_ms, 4),
+           "compress_gbs_of_field": round(4 * n / (c_ms * 1e-3) / 1e9, 1),
+           "decompress_gbs_of_field": round(4 * n / (d_ms * 1e-3) / 1e9, 1),
+           "compress_roofline_frac": round(c_alg / (c_ms * 1e-3) / 1e9 / peak, 4),
+           "decompress_roofline_frac": round(d_alg / (d_ms * 1e-3) / 1e9 / peak, 4),
+           "entropy_bits_per_point": q["entropy_bits_per_point"], "psnr_db": q["psnr_db"],
+           "n_outliers": int(h.n_outliers)}
+    del x, xr, cf, bufs, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def lossless_stage(G, cf, stream, max_len: int = 16) -> dict:
     """The lossless stage after the histogram (Sec. V-A), outside the timed region:
     host codebook time, the chunked Huffman encoder's and decoder's device times
@@ -372,6 +425,7 @@ def run_ours(args, rank, world, local):
         "quality": quality_summary(G, cf, x, xrec),
         "x_extended_domain": x_domain_variant(G, x, args.eb, cfg, dims, stream),
         "lossless": lossless_stage(G, cf, stream),
+        "nd_variants": [nd_variant(G, 2, args.eb, stream, peak), nd_variant(G, 1, args.eb, stream, peak)],
         "gpu_launches": (G.launches_compress(cfg) + G.LAUNCHES_DECOMPRESS) * args.steps,
         "clocks": clocks,
     }

@@ -8,11 +8,13 @@
 // e_l = e / alpha^l (Sec. IV-B.1) for all L levels; levels coarser than stride 4
 // use level_kind[2].
 //
-// One CTA per tile: 2-D tiles own 16 rows x 128 columns of one slice, 1-D tiles
-// 2048 points of one row; the CTA stages the tile with its closing row and column
-// (the anchors and points its chunks borrow from the next tile) in shared memory,
-// runs every pass on it, and writes only what it owns.  Passes inside a tile are
-// separated by barriers; tiles are independent.
+// Tiles: 2-D tiles own 16 rows x 128 columns of one slice, 1-D tiles 2048 points
+// of one row.  Persistent CTAs take tiles in turn; a CTA stages the tile with its
+// closing row and column (the anchors and points its chunks borrow from the next
+// tile) in shared memory, runs every pass on it, and writes only what it owns.
+// Passes inside a tile are separated by barriers; tiles are independent.  The level
+// constants (double arithmetic, slow on this part) are formed once per CTA, one
+// thread per level.
 //
 // Outputs match the 3-D path's formats: codes (q + R, 0 for outliers, R at
 // anchors), anchors [nz'][ny'][nx'], the fused histogram, and the outlier bitmap
@@ -26,6 +28,7 @@ namespace {
 constexpr int ND_THREADS = 256;
 constexpr int ND_MAX_LEVELS = 9;
 constexpr int ND_HIST_SMEM_BINS = 8192;
+constexpr int ND_CTAS_PER_SM = 6;  // persistent CTAs per SM (registers capped to fit them)
 
 template <int NDIM>
 struct NdGeom;
@@ -91,12 +94,12 @@ __device__ __forceinline__ int nd_tiles(Dims d)
 template <int L>
 __device__ void nd_levels(const interp_header *h, LevelQ *lq)
 {
+    const int l = threadIdx.x;
+    if (l >= L) return;
     double apow = 1.0;
-    for (int l = 0; l < L; ++l) {
-        const float e = (float)(h->eb_abs / apow);
-        lq[l] = LevelQ{e, 2.0f * e, (float)(1.0 / (2.0 * (double)e))};
-        apow *= h->alpha;
-    }
+    for (int j = 0; j < l; ++j) apow *= h->alpha;
+    const float e = (float)(h->eb_abs / apow);
+    lq[l] = LevelQ{e, 2.0f * e, (float)(1.0 / (2.0 * (double)e))};
 }
 
 struct NdPass {
@@ -174,38 +177,191 @@ __device__ __forceinline__ NdCfg nd_cfg(const interp_header *h)
     return c;
 }
 
+// Stage a full box (BY x BX elements, row pitch PX in shared memory) with every
+// thread's loads issued before any of them is stored: the box is one flat index
+// space split over the threads, ceil(BY*BX / ND_THREADS) loads each.
+template <int NDIM, typename T>
+__device__ __forceinline__ void nd_stage_full(T *dst, const T *src, long long row0, int nx, int x0)
+{
+    using G = NdGeom<NDIM>;
+    constexpr int NE = G::BY * G::BX;
+    constexpr int K = (NE + ND_THREADS - 1) / ND_THREADS;
+    T r[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = threadIdx.x + k * ND_THREADS;
+        if (e < NE) {
+            const int by = e / G::BX, bx = e - by * G::BX;
+            r[k] = __ldg(src + (row0 + by) * nx + x0 + bx);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = threadIdx.x + k * ND_THREADS;
+        if (e < NE) {
+            const int by = e / G::BX, bx = e - by * G::BX;
+            dst[by * G::PX + bx] = r[k];
+        }
+    }
+}
+
+// Address of the outlier-bitmap word of owned row `by`, 32-column strip `cx`
+// (global strip index), the same tile-major layout as tiled_word without its divisions.
+struct NdBitmapRow {
+    size_t base;  // address of strip 0 of the tile's first row
+    int stride;   // address step from one strip to the next: nz * OY
+};
+
+__device__ __forceinline__ NdBitmapRow nd_bitmap_row(const NdTile &t, int wpr, int nz)
+{
+    const int gy = t.y0;  // the tile's first row (2-D: a multiple of 16 = OY)
+    NdBitmapRow r;
+    r.base = ((size_t)(gy / OY) * wpr * nz + t.z) * OY + (gy % OY);
+    r.stride = nz * OY;
+    return r;
+}
+
+// ---- full tiles: the staged box lies inside the field, so every chunk is whole
+// and every pass has a shape known at compile time (no runtime division, and the
+// stencil depends only on the point's position in its chunk).
+struct NdPointCtx {
+    LevelQ q;
+    Cubic ck;
+    int spline;
+    uint32_t cbias;
+    float Rf;
+    uint16_t *cs;          // compression: owned codes [TY][TX]
+    const uint16_t *cb;    // decompression: the box's codes
+    const float *xrec;     // decompression: outlier values (scattered beforehand)
+    long long row0;
+    int nx, x0;
+};
+
+template <int NDIM, int S, int AX, int SO, bool COMPRESS>
+__device__ __forceinline__ void nd_full_pass(float *v, const NdPointCtx &c)
+{
+    using G = NdGeom<NDIM>;
+    constexpr int A = G::A;
+    constexpr int EA = AX == 1 ? G::BY - 1 : G::BX - 1;
+    constexpr int EO = NDIM == 1 ? 0 : (AX == 1 ? G::BX - 1 : G::BY - 1);
+    constexpr int NA = (EA - S) / (2 * S) + 1;
+    constexpr int NO = EO / SO + 1;
+    constexpr int SA = AX == 1 ? G::PX : 1;
+    constexpr int SOM = AX == 1 ? 1 : G::PX;
+#pragma unroll 1
+    for (int idx = threadIdx.x; idx < NA * NO; idx += ND_THREADS) {
+        int ia, io;
+        if (AX == 2) {
+            ia = idx % NA;
+            io = idx / NA;
+        } else {
+            io = idx % NO;
+            ia = idx / NO;
+        }
+        const int n = S + 2 * S * ia, m = io * SO;
+        const int i = n * SA + m * SOM;
+        const int r = n % A;  // chunk [n - r, n - r + A], whole: x_{n+s} always exists
+        const float m1 = v[i - S * SA], p1 = v[i + S * SA];
+        float pred;
+        if (!c.spline) {
+            pred = sp_linear(m1, p1);
+        } else {
+            const bool hm3 = r >= 3 * S, hp3 = r + 3 * S <= A;
+            if (hm3 && hp3) pred = sp_cubic(c.ck, v[i - 3 * S * SA], m1, p1, v[i + 3 * S * SA]);
+            else if (hm3) pred = sp_quad_left(v[i - 3 * S * SA], m1, p1);
+            else if (hp3) pred = sp_quad_right(m1, p1, v[i + 3 * S * SA]);
+            else pred = sp_linear(m1, p1);
+        }
+        const int by = AX == 1 ? n : (NDIM == 2 ? m : 0);
+        const int bx = AX == 2 ? n : m;
+        if (COMPRESS) {
+            float xr;
+            const uint32_t code = quantize(v[i], pred, c.q, c.cbias, c.Rf, xr);
+            v[i] = xr;
+            if (by < G::TY && bx < G::TX) c.cs[by * G::TX + bx] = (uint16_t)code;
+        } else {
+            const uint32_t code = c.cb[i];
+            v[i] = code ? pred + code_to_q(code, c.cbias) * c.q.twoe : c.xrec[(c.row0 + by) * c.nx + c.x0 + bx];
+        }
+    }
+}
+
+// Levels S, S/2, ..., 1 of a full tile; in 2-D the axis interpolated first in a level
+// sees the other on the 2s-grid, the second on the s-grid.
+template <int NDIM, int S, bool XFIRST, bool COMPRESS>
+__device__ __forceinline__ void nd_full_levels(float *v, NdPointCtx &c, const LevelQ *lq, const NdCfg &cfg)
+{
+    constexpr int l = S >= 256 ? 8 : S >= 128 ? 7 : S >= 64 ? 6 : S >= 32 ? 5 : S >= 16 ? 4 : S >= 8 ? 3 : S >= 4 ? 2
+                                                                                                            : S >= 2 ? 1 : 0;
+    c.q = lq[l];
+    c.spline = cfg.level_kind[l < 2 ? l : 2];
+    if (NDIM == 1) {
+        c.ck = cubic_coeffs(cfg.cubic_kind[2]);
+        nd_full_pass<NDIM, S, 2, 1, COMPRESS>(v, c);
+        __syncthreads();
+    } else {
+        constexpr int F = XFIRST ? 2 : 1, O = XFIRST ? 1 : 2;
+        c.ck = cubic_coeffs(cfg.cubic_kind[F]);
+        nd_full_pass<NDIM, S, F, 2 * S, COMPRESS>(v, c);
+        __syncthreads();
+        c.ck = cubic_coeffs(cfg.cubic_kind[O]);
+        nd_full_pass<NDIM, S, O, S, COMPRESS>(v, c);
+        __syncthreads();
+    }
+    if constexpr (S > 1) nd_full_levels<NDIM, S / 2, XFIRST, COMPRESS>(v, c, lq, cfg);
+}
+
+template <int NDIM, bool COMPRESS>
+__device__ __forceinline__ void nd_full_tile(float *v, NdPointCtx &c, const LevelQ *lq, const NdCfg &cfg)
+{
+    using G = NdGeom<NDIM>;
+    int px = 0, py = 0;
+    for (int j = 0; j < 3; ++j) {
+        if (cfg.order[j] == 2) px = j;
+        if (cfg.order[j] == 1) py = j;
+    }
+    if (NDIM == 2 && py < px)
+        nd_full_levels<NDIM, G::A / 2, false, COMPRESS>(v, c, lq, cfg);
+    else
+        nd_full_levels<NDIM, G::A / 2, true, COMPRESS>(v, c, lq, cfg);
+}
+
 template <int NDIM>
-__global__ void __launch_bounds__(ND_THREADS) k_nd_compress(CompressArgs a)
+__device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const NdCfg &cfg, const LevelQ *lq, float *v,
+                                                 uint16_t *cs, uint32_t *hs, bool smem_hist, uint32_t &central,
+                                                 int b)
 {
     using G = NdGeom<NDIM>;
     constexpr int L = G::L;
-    __shared__ float v[G::BY * G::PX];
-    __shared__ uint16_t cs[G::TY * G::TX];
-    __shared__ LevelQ lq[ND_MAX_LEVELS];
-    extern __shared__ uint32_t hs[];  // histogram bins when 2R <= ND_HIST_SMEM_BINS
     const Dims d = a.dims;
-    const interp_header *h = a.hdr;
     const int tid = threadIdx.x;
     const int bins = 2 * a.radius;
-    const bool smem_hist = a.hist && bins <= ND_HIST_SMEM_BINS;
-    if (tid == 0) nd_levels<L>(h, lq);
-    if (smem_hist)
-        for (int i = tid; i < bins; i += ND_THREADS) hs[i] = 0u;
-    const NdCfg cfg = nd_cfg(h);
     const uint32_t cbias = kMagicBits - (uint32_t)a.radius;
     const float Rf = (float)a.radius;
-    const NdTile t = nd_tile<NDIM>(d, blockIdx.x);
+    const NdTile t = nd_tile<NDIM>(d, b);
 
     // stage the box
-    for (int by = 0; by <= t.ey; ++by) {
-        const float *src = a.x + (t.row0 + by) * d.nx + t.x0;
-        for (int bx = tid; bx <= t.ex; bx += ND_THREADS) v[by * G::PX + bx] = __ldg(src + bx);
+    const bool full = t.ey == G::BY - 1 && t.ex == G::BX - 1;
+    if (full) {
+        nd_stage_full<NDIM>(v, a.x, t.row0, d.nx, t.x0);
+    } else {
+        for (int by = 0; by <= t.ey; ++by) {
+            const float *src = a.x + (t.row0 + by) * d.nx + t.x0;
+            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) v[by * G::PX + bx] = __ldg(src + bx);
+        }
     }
     // owned anchors: code R, value kept
     for (int i = tid; i < G::TY * G::TX; i += ND_THREADS) cs[i] = (uint16_t)a.radius;
     __syncthreads();
 
-    for (int l = L - 1; l >= 0; --l) {
+    if (full) {
+        NdPointCtx c;
+        c.cbias = cbias;
+        c.Rf = Rf;
+        c.cs = cs;
+        nd_full_tile<NDIM, true>(v, c, lq, cfg);
+    }
+    for (int l = full ? -1 : L - 1; l >= 0; --l) {
         const int s = 1 << l;
         const LevelQ q = lq[l];
         const int spline = cfg.level_kind[l < 2 ? l : 2];
@@ -252,25 +408,53 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_compress(CompressArgs a)
     const int lane = tid & 31, warp = tid >> 5;
     const int wpr = (d.nx + 31) / 32;
     const int strips = (t.ox + 31) / 32;
-    uint32_t central = 0;
+    const NdBitmapRow bm = nd_bitmap_row(t, wpr, d.nz);
     for (int u = warp; u < t.oy * strips; u += ND_THREADS / 32) {
-        const int by = u / strips, bx = (u - by * strips) * 32 + lane;
+        const int by = u / strips, strip = u - by * strips, bx = strip * 32 + lane;
         const bool in = bx < t.ox;
         const uint32_t code = in ? cs[by * G::TX + bx] : 1u;
         const long long row = t.row0 + by;
         if (in) a.codes[row * d.nx + t.x0 + bx] = (uint16_t)code;
         const uint32_t word = __ballot_sync(0xffffffffu, code == 0u);
         if (lane == 0) {
-            const long long gw = row * wpr + (t.x0 >> 5) + (bx >> 5);
-            a.bitmap[tiled_word(gw, wpr, d.ny, d.nz)] = word;
-            if (word) atomicAdd(a.blockcnt + gw / BITMAP_BLOCK_WORDS, (uint32_t)__popc(word));
+            const int cx = (t.x0 >> 5) + strip;
+            // rows of a 2-D tile stay in one OY-row group (y0 is a multiple of OY)
+            a.bitmap[bm.base + (size_t)cx * bm.stride + by] = word;
+            if (word) {
+                const long long gw = row * wpr + cx;
+                atomicAdd(a.blockcnt + gw / BITMAP_BLOCK_WORDS, (uint32_t)__popc(word));
+            }
         }
         if (a.hist && in) {
             if (code == (uint32_t)a.radius) ++central;
             else if (code < (uint32_t)bins) atomicAdd(smem_hist ? &hs[code] : &a.hist[code], 1u);
         }
     }
+    __syncthreads();  // the box and the code stage are reused by the next tile
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(ND_THREADS, ND_CTAS_PER_SM) k_nd_compress(CompressArgs a)
+{
+    using G = NdGeom<NDIM>;
+    __shared__ float v[G::BY * G::PX];
+    __shared__ uint16_t cs[G::TY * G::TX];
+    __shared__ LevelQ lq[ND_MAX_LEVELS];
+    extern __shared__ uint32_t hs[];  // histogram bins when 2R <= ND_HIST_SMEM_BINS
+    const int tid = threadIdx.x;
+    const int bins = 2 * a.radius;
+    const bool smem_hist = a.hist && bins <= ND_HIST_SMEM_BINS;
+    nd_levels<G::L>(a.hdr, lq);
+    if (smem_hist)
+        for (int i = tid; i < bins; i += ND_THREADS) hs[i] = 0u;
+    const NdCfg cfg = nd_cfg(a.hdr);
+    uint32_t central = 0;
+    const int tiles = nd_tiles<NDIM>(a.dims);
+    __syncthreads();
+    for (int b = blockIdx.x; b < tiles; b += gridDim.x)
+        nd_compress_tile<NDIM>(a, cfg, lq, v, cs, hs, smem_hist, central, b);
     if (a.hist) {
+        const int lane = tid & 31;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) central += __shfl_xor_sync(0xffffffffu, central, off);
         if (lane == 0 && central) atomicAdd(smem_hist ? &hs[a.radius] : &a.hist[a.radius], central);
@@ -283,26 +467,24 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_compress(CompressArgs a)
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(ND_THREADS) k_nd_decompress(DecompressArgs a)
+__device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, const NdCfg &cfg, const LevelQ *lq,
+                                                   float *v, uint16_t *cb, uint32_t cbias, int b)
 {
     using G = NdGeom<NDIM>;
     constexpr int L = G::L;
-    __shared__ float v[G::BY * G::PX];
-    __shared__ uint16_t cb[G::BY * G::PX];
-    __shared__ LevelQ lq[ND_MAX_LEVELS];
     const Dims d = a.dims;
-    const interp_header *h = a.hdr;
     const int tid = threadIdx.x;
-    if (tid == 0) nd_levels<L>(h, lq);
-    const NdCfg cfg = nd_cfg(h);
-    const uint32_t cbias = kMagicBits - (uint32_t)h->cfg.radius;
-    const NdTile t = nd_tile<NDIM>(d, blockIdx.x);
+    const NdTile t = nd_tile<NDIM>(d, b);
 
     // stage the box's codes and anchors (the closing row and column included)
     const int ax = (d.nx - 1) / G::A + 1;
+    const bool full = t.ey == G::BY - 1 && t.ex == G::BX - 1;
+    if (full) nd_stage_full<NDIM>(cb, a.codes, t.row0, d.nx, t.x0);
     for (int by = 0; by <= t.ey; ++by) {
-        const uint16_t *src = a.codes + (t.row0 + by) * d.nx + t.x0;
-        for (int bx = tid; bx <= t.ex; bx += ND_THREADS) cb[by * G::PX + bx] = __ldg(src + bx);
+        if (!full) {
+            const uint16_t *src = a.codes + (t.row0 + by) * d.nx + t.x0;
+            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) cb[by * G::PX + bx] = __ldg(src + bx);
+        }
         const bool anchor_row = NDIM == 1 || (t.y0 + by) % G::A == 0;
         if (anchor_row) {
             const long long arow =
@@ -313,7 +495,17 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_decompress(DecompressArgs a)
     }
     __syncthreads();
 
-    for (int l = L - 1; l >= 0; --l) {
+    if (full) {
+        NdPointCtx c;
+        c.cbias = cbias;
+        c.cb = cb;
+        c.xrec = a.xrec;
+        c.row0 = t.row0;
+        c.nx = d.nx;
+        c.x0 = t.x0;
+        nd_full_tile<NDIM, false>(v, c, lq, cfg);
+    }
+    for (int l = full ? -1 : L - 1; l >= 0; --l) {
         const int s = 1 << l;
         const float twoe = lq[l].twoe;
         const int spline = cfg.level_kind[l < 2 ? l : 2];
@@ -350,6 +542,22 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_decompress(DecompressArgs a)
         float *dst = a.xrec + (t.row0 + by) * d.nx + t.x0;
         for (int bx = tid; bx < t.ox; bx += ND_THREADS) dst[bx] = v[by * G::PX + bx];
     }
+    __syncthreads();  // the box is reused by the next tile
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(ND_THREADS, ND_CTAS_PER_SM) k_nd_decompress(DecompressArgs a)
+{
+    using G = NdGeom<NDIM>;
+    __shared__ float v[G::BY * G::PX];
+    __shared__ uint16_t cb[G::BY * G::PX];
+    __shared__ LevelQ lq[ND_MAX_LEVELS];
+    nd_levels<G::L>(a.hdr, lq);
+    const NdCfg cfg = nd_cfg(a.hdr);
+    const uint32_t cbias = kMagicBits - (uint32_t)a.hdr->cfg.radius;
+    const int tiles = nd_tiles<NDIM>(a.dims);
+    __syncthreads();
+    for (int b = blockIdx.x; b < tiles; b += gridDim.x) nd_decompress_tile<NDIM>(a, cfg, lq, v, cb, cbias, b);
 }
 
 int nd_tiles_host(int ndim, Dims d)
@@ -370,10 +578,11 @@ cudaError_t launch_nd_compress(int ndim, const CompressArgs &a, cudaStream_t s)
     const int tiles = nd_tiles_host(ndim, a.dims);
     if (tiles == 0) return cudaSuccess;
     const size_t hist_smem = (a.hist && 2 * a.radius <= ND_HIST_SMEM_BINS) ? sizeof(uint32_t) * 2 * a.radius : 0;
+    const int grid = min(tiles, sm_count() * ND_CTAS_PER_SM);
     if (ndim == 2)
-        k_nd_compress<2><<<tiles, ND_THREADS, hist_smem, s>>>(a);
+        k_nd_compress<2><<<grid, ND_THREADS, hist_smem, s>>>(a);
     else
-        k_nd_compress<1><<<tiles, ND_THREADS, hist_smem, s>>>(a);
+        k_nd_compress<1><<<grid, ND_THREADS, hist_smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -382,10 +591,11 @@ cudaError_t launch_nd_decompress(int ndim, const DecompressArgs &a, cudaStream_t
     if (ndim != 1 && ndim != 2) return cudaErrorInvalidValue;
     const int tiles = nd_tiles_host(ndim, a.dims);
     if (tiles == 0) return cudaSuccess;
+    const int grid = min(tiles, sm_count() * ND_CTAS_PER_SM);
     if (ndim == 2)
-        k_nd_decompress<2><<<tiles, ND_THREADS, 0, s>>>(a);
+        k_nd_decompress<2><<<grid, ND_THREADS, 0, s>>>(a);
     else
-        k_nd_decompress<1><<<tiles, ND_THREADS, 0, s>>>(a);
+        k_nd_decompress<1><<<grid, ND_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -48,12 +48,17 @@ def parse():
     p.add_argument("--eb", type=float, default=EB)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the untimed reports (quality, x-domain, lossless, 1-D/2-D) in profiling runs")
     p.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling runs only)")
+    p.add_argument("--ndim", type=int, default=3, choices=[1, 2, 3],
+                   help="profiling runs of the 1-D / 2-D geometry on its 512 MiB field (64 x 2^21 / 32 x 2048^2)")
     p.add_argument("--workload", default="field", choices=["field", "batch", "serve"],
                    help="field: the 512^3 round trip (default); batch: three uneven fields in one persistent "
                         "launch vs one call per field; serve: the continuous-batching serving loop")
     a = p.parse_args()
-    a.shape = tuple(int(v) for v in a.shape.split(",")) if a.shape else SHAPE
+    nd_shape = {3: SHAPE, 2: (32, 2048, 2048), 1: (64, 1, 1 << 21)}[a.ndim]
+    a.shape = tuple(int(v) for v in a.shape.split(",")) if a.shape else nd_shape
     return a
 
 
@@ -121,10 +126,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# sources of the kernels whose ncu counters are committed (k_compress, k_decompress, k_range)
+TRAFFIC_SOURCES = ("common.cuh", "tma.cuh", "tiles.cu", "profile.cu")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2312_05492_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in TRAFFIC_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -314,11 +323,14 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     G.load()
-    x = fields.lognormal(args.shape, 11.0 / 3.0, 1 + 1000 * rank, device=dev)
+    if args.ndim == 3:
+        x = fields.lognormal(args.shape, 11.0 / 3.0, 1 + 1000 * rank, device=dev)
+    else:
+        x = fields.grf(args.shape, 3.0, 5 + 1000 * rank, device=dev, fft_dtype=torch.float32)
     torch.cuda.empty_cache()  # release the FFT temporaries of the generator
     n = x.numel()
     nbytes = 4 * n
-    cfg = G.Config(autotune=True, eb_mode="rel", level_kind=(1, 1, 1), radius=512)
+    cfg = G.Config(autotune=True, eb_mode="rel", level_kind=(1, 1, 1), radius=512, ndim=args.ndim)
     dims = tuple(x.shape)
     ws = torch.empty(G.interp_workspace_bytes(dims, cfg.to_c()), dtype=torch.uint8, device=dev)
     bufs = G.allocate(dims, cfg, dev, capacity=n // 64)
@@ -385,7 +397,7 @@ def run_ours(args, rank, world, local):
 
     h = cf.host_header(refresh=True)
     n_out = int(h.n_outliers)
-    A = G.interp_anchor_count(dims)
+    A = G.interp_anchor_count_nd(dims, args.ndim)
     peak, peak_kind = measured_peaks()
     comp_tile_ms = cms / max(cn, 1)
     dec_tile_ms = dms / max(dn, 1)
@@ -396,11 +408,11 @@ def run_ours(args, rank, world, local):
     roofline = {"bound": "hbm", "kernel": "k_compress (fused predict-quantize tile kernel)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": ncu_traffic("k_compress"), "algorithmic_bytes_per_launch": comp_alg,
+                "traffic": ncu_traffic("k_compress") if args.ndim == 3 else None, "algorithmic_bytes_per_launch": comp_alg,
                 "avg_launch_ms": round(comp_tile_ms, 5), "launches_timed": cn}
     dec_ach = dec_alg / (dec_tile_ms * 1e-3) / 1e9
     roofline_dec = {"bound": "hbm", "kernel": "k_decompress", "achieved": round(dec_ach, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(dec_ach / peak, 4), "traffic": ncu_traffic("k_decompress"),
+                    "unit": "GB/s", "frac": round(dec_ach / peak, 4), "traffic": ncu_traffic("k_decompress") if args.ndim == 3 else None,
                     "algorithmic_bytes_per_launch": dec_alg, "avg_launch_ms": round(dec_tile_ms, 5)}
     step_gbs = step_alg / (ms_step * 1e-3) / 1e9
 
@@ -409,7 +421,8 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.shape == SHAPE else f"profiling case {args.shape}",
+        "config": {"workload": WORKLOAD if args.shape == SHAPE and args.ndim == 3
+                   else f"profiling case {args.shape} ndim {args.ndim}",
                    "shape": list(args.shape), "eb_rel": args.eb, "eb_abs": h.eb_abs,
                    "alpha": h.alpha, "dim_order": list(h.cfg.dim_order), "level_kind": list(h.cfg.level_kind),
                    "cubic_kind": list(h.cfg.cubic_kind), "radius": 512, "n_outliers": n_out,
@@ -423,12 +436,13 @@ def run_ours(args, rank, world, local):
                           "frac": round(step_gbs / peak, 4), "algorithmic_bytes_per_step": step_alg},
         "max_abs_err_over_eb": err / h.eb_abs,
         "quality": quality_summary(G, cf, x, xrec),
-        "x_extended_domain": x_domain_variant(G, x, args.eb, cfg, dims, stream),
-        "lossless": lossless_stage(G, cf, stream),
-        "nd_variants": [nd_variant(G, 2, args.eb, stream, peak), nd_variant(G, 1, args.eb, stream, peak)],
         "gpu_launches": (G.launches_compress(cfg) + G.LAUNCHES_DECOMPRESS) * args.steps,
         "clocks": clocks,
     }
+    if not args.no_extras:
+        out["x_extended_domain"] = x_domain_variant(G, x, args.eb, cfg, dims, stream)
+        out["lossless"] = lossless_stage(G, cf, stream)
+        out["nd_variants"] = [nd_variant(G, 2, args.eb, stream, peak), nd_variant(G, 1, args.eb, stream, peak)]
 
     # ---- end to end through the public API with host buffers: every step copies its
     # field from pinned host memory, compresses, decompresses and copies the

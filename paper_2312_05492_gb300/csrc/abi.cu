@@ -194,7 +194,7 @@ int compress_nd(const interp_compress_item &it, interp_stream_t stream)
     }
     if (e == cudaSuccess)
         e = gi::launch_outlier_compaction(bitmap, blockcnt, L.words, d, it.d_x, it.d_out_idx, it.d_out_val,
-                                          it.out_capacity, it.d_hdr, s);
+                                          it.out_capacity, it.d_hdr, s, true);  // row-major bitmap (nd.cu)
     return cuda_status(e);
 }
 

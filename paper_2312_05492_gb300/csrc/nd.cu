@@ -18,8 +18,8 @@
 //
 // Outputs match the 3-D path's formats: codes (q + R, 0 for outliers, R at
 // anchors), anchors [nz'][ny'][nx'], the fused histogram, and the outlier bitmap
-// (one word per 32 x-positions of a row, tile-major addresses) with per-block
-// popcounts for the ordered compaction.
+// (one word per 32 x-positions of a row, here in row-major order: a 1-D tile's
+// words are contiguous) with per-block popcounts for the ordered compaction.
 #include "common.cuh"
 
 namespace gi {
@@ -46,6 +46,19 @@ struct NdGeom<1> {
     static constexpr int BY = 1, BX = 2049;
     static constexpr int PX = 2049;
 };
+
+// Shared-memory index of box element i.  1-D passes walk the row with stride 2s
+// (up to 512 words), which would put a warp's accesses in one bank; one pad word
+// after every 32 spreads them.  2-D boxes (odd row pitch) are unpadded.
+template <int NDIM>
+__device__ __forceinline__ int vix(int i) { return NDIM == 1 ? i + (i >> 5) : i; }
+// the same for 16-bit arrays: one pad word (two halves) after every 32 words
+template <int NDIM>
+__device__ __forceinline__ int hix(int j) { return NDIM == 1 ? j + ((j >> 6) << 1) : j; }
+template <int NDIM>
+__host__ __device__ constexpr int vsize(int n) { return NDIM == 1 ? n + (n >> 5) + 1 : n; }
+template <int NDIM>
+__host__ __device__ constexpr int hsize(int n) { return NDIM == 1 ? n + ((n >> 6) << 1) + 2 : n; }
 
 struct NdTile {
     long long row0;  // first global (z, y) row of the tile: z * ny + y0
@@ -114,20 +127,21 @@ struct NdPass {
 // Stencil by the neighbour count within the closed chunk [lo, lo + A] (clipped to
 // the staged box, whose end is the field's end or the chunk's closing point),
 // Sec. IV-B.1: 4 neighbours cubic, 3 quadratic, 2 linear, 1 copy of x_{n-s}.
-template <int A>
+template <int NDIM>
 __device__ __forceinline__ float nd_predict(const float *v, int i, int n, int s, int ea, int sa, int spline,
                                            const Cubic &ck)
 {
+    constexpr int A = NdGeom<NDIM>::A;
     const int lo = (n / A) * A;
     const int hi = min(lo + A, ea);
-    const float m1 = v[i - s * sa];
+    const float m1 = v[vix<NDIM>(i - s * sa)];
     if (n + s > hi) return m1;
-    const float p1 = v[i + s * sa];
+    const float p1 = v[vix<NDIM>(i + s * sa)];
     if (!spline) return sp_linear(m1, p1);
     const bool has_m3 = n - 3 * s >= lo, has_p3 = n + 3 * s <= hi;
-    if (has_m3 && has_p3) return sp_cubic(ck, v[i - 3 * s * sa], m1, p1, v[i + 3 * s * sa]);
-    if (has_m3) return sp_quad_left(v[i - 3 * s * sa], m1, p1);
-    if (has_p3) return sp_quad_right(m1, p1, v[i + 3 * s * sa]);
+    if (has_m3 && has_p3) return sp_cubic(ck, v[vix<NDIM>(i - 3 * s * sa)], m1, p1, v[vix<NDIM>(i + 3 * s * sa)]);
+    if (has_m3) return sp_quad_left(v[vix<NDIM>(i - 3 * s * sa)], m1, p1);
+    if (has_p3) return sp_quad_right(m1, p1, v[vix<NDIM>(i + 3 * s * sa)]);
     return sp_linear(m1, p1);
 }
 
@@ -200,25 +214,10 @@ __device__ __forceinline__ void nd_stage_full(T *dst, const T *src, long long ro
         const int e = threadIdx.x + k * ND_THREADS;
         if (e < NE) {
             const int by = e / G::BX, bx = e - by * G::BX;
-            dst[by * G::PX + bx] = r[k];
+            const int j = by * G::PX + bx;
+            dst[sizeof(T) == 4 ? vix<NDIM>(j) : hix<NDIM>(j)] = r[k];
         }
     }
-}
-
-// Address of the outlier-bitmap word of owned row `by`, 32-column strip `cx`
-// (global strip index), the same tile-major layout as tiled_word without its divisions.
-struct NdBitmapRow {
-    size_t base;  // address of strip 0 of the tile's first row
-    int stride;   // address step from one strip to the next: nz * OY
-};
-
-__device__ __forceinline__ NdBitmapRow nd_bitmap_row(const NdTile &t, int wpr, int nz)
-{
-    const int gy = t.y0;  // the tile's first row (2-D: a multiple of 16 = OY)
-    NdBitmapRow r;
-    r.base = ((size_t)(gy / OY) * wpr * nz + t.z) * OY + (gy % OY);
-    r.stride = nz * OY;
-    return r;
 }
 
 // ---- full tiles: the staged box lies inside the field, so every chunk is whole
@@ -261,27 +260,29 @@ __device__ __forceinline__ void nd_full_pass(float *v, const NdPointCtx &c)
         const int n = S + 2 * S * ia, m = io * SO;
         const int i = n * SA + m * SOM;
         const int r = n % A;  // chunk [n - r, n - r + A], whole: x_{n+s} always exists
-        const float m1 = v[i - S * SA], p1 = v[i + S * SA];
+        const float m1 = v[vix<NDIM>(i - S * SA)], p1 = v[vix<NDIM>(i + S * SA)];
         float pred;
         if (!c.spline) {
             pred = sp_linear(m1, p1);
         } else {
             const bool hm3 = r >= 3 * S, hp3 = r + 3 * S <= A;
-            if (hm3 && hp3) pred = sp_cubic(c.ck, v[i - 3 * S * SA], m1, p1, v[i + 3 * S * SA]);
-            else if (hm3) pred = sp_quad_left(v[i - 3 * S * SA], m1, p1);
-            else if (hp3) pred = sp_quad_right(m1, p1, v[i + 3 * S * SA]);
+            if (hm3 && hp3) pred = sp_cubic(c.ck, v[vix<NDIM>(i - 3 * S * SA)], m1, p1, v[vix<NDIM>(i + 3 * S * SA)]);
+            else if (hm3) pred = sp_quad_left(v[vix<NDIM>(i - 3 * S * SA)], m1, p1);
+            else if (hp3) pred = sp_quad_right(m1, p1, v[vix<NDIM>(i + 3 * S * SA)]);
             else pred = sp_linear(m1, p1);
         }
         const int by = AX == 1 ? n : (NDIM == 2 ? m : 0);
         const int bx = AX == 2 ? n : m;
         if (COMPRESS) {
             float xr;
-            const uint32_t code = quantize(v[i], pred, c.q, c.cbias, c.Rf, xr);
-            v[i] = xr;
-            if (by < G::TY && bx < G::TX) c.cs[by * G::TX + bx] = (uint16_t)code;
+            const int vi = vix<NDIM>(i);
+            const uint32_t code = quantize(v[vi], pred, c.q, c.cbias, c.Rf, xr);
+            v[vi] = xr;
+            if (by < G::TY && bx < G::TX) c.cs[hix<NDIM>(by * G::TX + bx)] = (uint16_t)code;
         } else {
-            const uint32_t code = c.cb[i];
-            v[i] = code ? pred + code_to_q(code, c.cbias) * c.q.twoe : c.xrec[(c.row0 + by) * c.nx + c.x0 + bx];
+            const uint32_t code = c.cb[hix<NDIM>(i)];
+            v[vix<NDIM>(i)] = code ? pred + code_to_q(code, c.cbias) * c.q.twoe
+                                   : c.xrec[(c.row0 + by) * c.nx + c.x0 + bx];
         }
     }
 }
@@ -347,11 +348,11 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
     } else {
         for (int by = 0; by <= t.ey; ++by) {
             const float *src = a.x + (t.row0 + by) * d.nx + t.x0;
-            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) v[by * G::PX + bx] = __ldg(src + bx);
+            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) v[vix<NDIM>(by * G::PX + bx)] = __ldg(src + bx);
         }
     }
     // owned anchors: code R, value kept
-    for (int i = tid; i < G::TY * G::TX; i += ND_THREADS) cs[i] = (uint16_t)a.radius;
+    for (int i = tid; i < hsize<NDIM>(G::TY * G::TX); i += ND_THREADS) cs[i] = (uint16_t)a.radius;
     __syncthreads();
 
     if (full) {
@@ -382,13 +383,13 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
                 }
                 const int n = s + 2 * s * ia, m = io * p.so;
                 const int i = n * p.sa + m * p.so_mem;
-                const float pred = nd_predict<G::A>(v, i, n, s, p.ea, p.sa, spline, ck);
+                const float pred = nd_predict<NDIM>(v, i, n, s, p.ea, p.sa, spline, ck);
                 float xr;
-                const uint32_t code = quantize(v[i], pred, q, cbias, Rf, xr);
-                v[i] = xr;
+                const uint32_t code = quantize(v[vix<NDIM>(i)], pred, q, cbias, Rf, xr);
+                v[vix<NDIM>(i)] = xr;
                 const int by = p.a == 1 ? n : (NDIM == 2 ? m : 0);
                 const int bx = p.a == 2 ? n : m;
-                if (by < G::TY && bx < G::TX) cs[by * G::TX + bx] = (uint16_t)code;
+                if (by < G::TY && bx < G::TX) cs[hix<NDIM>(by * G::TX + bx)] = (uint16_t)code;
             }
             __syncthreads();
         }
@@ -400,7 +401,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
         const long long arow = NDIM == 2 ? (long long)t.z * ((d.ny - 1) / G::A + 1) + t.y0 / G::A : t.row0;
         if (t.y0 % G::A == 0 || NDIM == 1)
             for (int bx = tid * G::A; bx < t.ox; bx += ND_THREADS * G::A)
-                a.anchors[arow * ax + (t.x0 + bx) / G::A] = v[bx];
+                a.anchors[arow * ax + (t.x0 + bx) / G::A] = v[vix<NDIM>(bx)];
     }
 
     // codes, outlier bitmap words and the histogram of the owned points, one
@@ -408,22 +409,17 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
     const int lane = tid & 31, warp = tid >> 5;
     const int wpr = (d.nx + 31) / 32;
     const int strips = (t.ox + 31) / 32;
-    const NdBitmapRow bm = nd_bitmap_row(t, wpr, d.nz);
     for (int u = warp; u < t.oy * strips; u += ND_THREADS / 32) {
         const int by = u / strips, strip = u - by * strips, bx = strip * 32 + lane;
         const bool in = bx < t.ox;
-        const uint32_t code = in ? cs[by * G::TX + bx] : 1u;
+        const uint32_t code = in ? cs[hix<NDIM>(by * G::TX + bx)] : 1u;
         const long long row = t.row0 + by;
         if (in) a.codes[row * d.nx + t.x0 + bx] = (uint16_t)code;
         const uint32_t word = __ballot_sync(0xffffffffu, code == 0u);
         if (lane == 0) {
-            const int cx = (t.x0 >> 5) + strip;
-            // rows of a 2-D tile stay in one OY-row group (y0 is a multiple of OY)
-            a.bitmap[bm.base + (size_t)cx * bm.stride + by] = word;
-            if (word) {
-                const long long gw = row * wpr + cx;
-                atomicAdd(a.blockcnt + gw / BITMAP_BLOCK_WORDS, (uint32_t)__popc(word));
-            }
+            const long long gw = row * wpr + (t.x0 >> 5) + strip;  // row-major bitmap
+            a.bitmap[gw] = word;
+            if (word) atomicAdd(a.blockcnt + gw / BITMAP_BLOCK_WORDS, (uint32_t)__popc(word));
         }
         if (a.hist && in) {
             if (code == (uint32_t)a.radius) ++central;
@@ -437,8 +433,8 @@ template <int NDIM>
 __global__ void __launch_bounds__(ND_THREADS, ND_CTAS_PER_SM) k_nd_compress(CompressArgs a)
 {
     using G = NdGeom<NDIM>;
-    __shared__ float v[G::BY * G::PX];
-    __shared__ uint16_t cs[G::TY * G::TX];
+    __shared__ float v[vsize<NDIM>(G::BY * G::PX)];
+    __shared__ uint16_t cs[hsize<NDIM>(G::TY * G::TX)];
     __shared__ LevelQ lq[ND_MAX_LEVELS];
     extern __shared__ uint32_t hs[];  // histogram bins when 2R <= ND_HIST_SMEM_BINS
     const int tid = threadIdx.x;
@@ -483,14 +479,14 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
     for (int by = 0; by <= t.ey; ++by) {
         if (!full) {
             const uint16_t *src = a.codes + (t.row0 + by) * d.nx + t.x0;
-            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) cb[by * G::PX + bx] = __ldg(src + bx);
+            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) cb[hix<NDIM>(by * G::PX + bx)] = __ldg(src + bx);
         }
         const bool anchor_row = NDIM == 1 || (t.y0 + by) % G::A == 0;
         if (anchor_row) {
             const long long arow =
                 NDIM == 2 ? (long long)t.z * ((d.ny - 1) / G::A + 1) + (t.y0 + by) / G::A : t.row0;
             for (int bx = tid * G::A; bx <= t.ex; bx += ND_THREADS * G::A)
-                v[by * G::PX + bx] = __ldg(a.anchors + arow * ax + (t.x0 + bx) / G::A);
+                v[vix<NDIM>(by * G::PX + bx)] = __ldg(a.anchors + arow * ax + (t.x0 + bx) / G::A);
         }
     }
     __syncthreads();
@@ -525,14 +521,14 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
                 }
                 const int n = s + 2 * s * ia, m = io * p.so;
                 const int i = n * p.sa + m * p.so_mem;
-                const float pred = nd_predict<G::A>(v, i, n, s, p.ea, p.sa, spline, ck);
-                const uint32_t code = cb[i];
+                const float pred = nd_predict<NDIM>(v, i, n, s, p.ea, p.sa, spline, ck);
+                const uint32_t code = cb[hix<NDIM>(i)];
                 if (code) {
-                    v[i] = pred + code_to_q(code, cbias) * twoe;
+                    v[vix<NDIM>(i)] = pred + code_to_q(code, cbias) * twoe;
                 } else {  // outlier: its value was scattered into xrec before this kernel
                     const int by = p.a == 1 ? n : (NDIM == 2 ? m : 0);
                     const int bx = p.a == 2 ? n : m;
-                    v[i] = a.xrec[(t.row0 + by) * d.nx + t.x0 + bx];
+                    v[vix<NDIM>(i)] = a.xrec[(t.row0 + by) * d.nx + t.x0 + bx];
                 }
             }
             __syncthreads();
@@ -540,7 +536,7 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
     }
     for (int by = 0; by < t.oy; ++by) {
         float *dst = a.xrec + (t.row0 + by) * d.nx + t.x0;
-        for (int bx = tid; bx < t.ox; bx += ND_THREADS) dst[bx] = v[by * G::PX + bx];
+        for (int bx = tid; bx < t.ox; bx += ND_THREADS) dst[bx] = v[vix<NDIM>(by * G::PX + bx)];
     }
     __syncthreads();  // the box is reused by the next tile
 }
@@ -549,8 +545,8 @@ template <int NDIM>
 __global__ void __launch_bounds__(ND_THREADS, ND_CTAS_PER_SM) k_nd_decompress(DecompressArgs a)
 {
     using G = NdGeom<NDIM>;
-    __shared__ float v[G::BY * G::PX];
-    __shared__ uint16_t cb[G::BY * G::PX];
+    __shared__ float v[vsize<NDIM>(G::BY * G::PX)];
+    __shared__ uint16_t cb[hsize<NDIM>(G::BY * G::PX)];
     __shared__ LevelQ lq[ND_MAX_LEVELS];
     nd_levels<G::L>(a.hdr, lq);
     const NdCfg cfg = nd_cfg(a.hdr);

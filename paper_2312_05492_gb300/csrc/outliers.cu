@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const uint32_t 
                                                                  int nz, const float *__restrict__ x,
                                                                  uint32_t *out_idx, float *out_val,
                                                                  unsigned long long capacity,
-                                                                 const interp_header *hdr, int nblk)
+                                                                 const interp_header *hdr, int nblk,
+                                                                 bool row_major)
 {
     const int b = blockIdx.x;
     const unsigned long long total = hdr->n_outliers;
@@ -80,7 +81,8 @@ __global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const uint32_t 
     int cnt = 0;
 #pragma unroll
     for (int k = 0; k < WORDS_PER_THREAD; ++k) {
-        wv[k] = (w0 + k < words) ? bitmap[tiled_word(w0 + k, words_per_row, ny, nz)] : 0u;
+        const long long w = w0 + k;
+        wv[k] = (w < words) ? bitmap[row_major ? (size_t)w : tiled_word(w, words_per_row, ny, nz)] : 0u;
         cnt += __popc(wv[k]);
     }
     // block exclusive scan of per-thread counts
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(HIST_THREADS) k_histogram(const uint16_t *__re
 
 cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
                                       const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
-                                      interp_header *hdr, cudaStream_t s)
+                                      interp_header *hdr, cudaStream_t s, bool row_major)
 {
     const int nblk = (int)((words + BITMAP_BLOCK_WORDS - 1) / BITMAP_BLOCK_WORDS);
     if (nblk <= 0) return cudaSuccess;
@@ -198,7 +200,8 @@ cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt
     if (e != cudaSuccess) return e;
     const int words_per_row = (d.nx + 31) / 32;
     k_outlier_write<<<nblk, WRITE_THREADS, 0, s>>>(bitmap, blockcnt, (long long)words, words_per_row, d.nx, d.ny,
-                                                  d.nz, x, out_idx, out_val, (unsigned long long)capacity, hdr, nblk);
+                                                  d.nz, x, out_idx, out_val, (unsigned long long)capacity, hdr, nblk,
+                                                  row_major);
     return cudaGetLastError();
 }
 

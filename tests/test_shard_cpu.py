@@ -108,19 +108,37 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("case", sorted(CASES))
-def test_sharded_equals_single_field(case):
-    world = 2
+def _run_world(case, world=2):
+    """One gloo job of `world` spawned ranks; None if the rendezvous or a rank failed
+    (the free port can be taken by another process between its probe and its use)."""
+    import queue
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
     procs = [ctx.Process(target=_worker, args=(r, world, port, case, q)) for r in range(world)]
     for p in procs:
         p.start()
-    full, xr_all, eb_abs, alpha, n_out = q.get(timeout=120)
+    try:
+        res = q.get(timeout=120)
+    except queue.Empty:
+        res = None
     for p in procs:
         p.join(timeout=60)
-        assert p.exitcode == 0
+        if p.is_alive():
+            p.kill()
+            p.join()
+        if p.exitcode != 0:
+            res = None
+    return res
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_sharded_equals_single_field(case):
+    res = _run_world(case)
+    if res is None:  # one retry on a fresh port
+        res = _run_world(case)
+    assert res is not None, "the world-2 gloo job failed twice"
+    full, xr_all, eb_abs, alpha, n_out = res
     dims, kind, eps, mode, cfg = CASES[case]
     x = _field(kind, dims)
     ref_eb, e, twoe, inv2e = O.bounds_for(x, eps, mode)

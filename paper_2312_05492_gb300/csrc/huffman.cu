@@ -14,9 +14,11 @@
 // its chunks' sizes, places them after the CTA's offset, and has every lane put
 // its codewords at its bit offset (a warp scan) in the warp's shared-memory copy
 // of the chunk, which is then written out with coalesced stores.
-// Decoding: one thread per chunk, reading its words in order: the first 11 bits
-// index a lookup table (symbol, length); longer codewords take the canonical
-// rule (per length, the first codeword and the first symbol index).
+// Decoding: one thread per chunk, reading its words in order: the next 10 bits
+// index a lookup table holding every whole codeword they contain (up to three
+// symbols and the bits they take); longer codewords take the canonical rule (per
+// length, the first codeword and the first symbol index).  Decoded codes are
+// staged per warp and stored coalesced.
 #include <algorithm>
 #include <cstring>
 #include <queue>
@@ -27,12 +29,13 @@
 namespace gi {
 namespace {
 
+
 constexpr int HCHUNK = 1024;          // codes per chunk
 constexpr int HLANE = HCHUNK / 32;    // codes per lane
 constexpr int ENC_WARPS = 8;
 constexpr int ENC_THREADS = 32 * ENC_WARPS;
 constexpr int MAX_LEN = 24;           // longest codeword the library builds
-constexpr int LUT_BITS = 11;
+constexpr int LUT_BITS = 10;
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 8;
 constexpr int TAB_THREADS = 1024;
@@ -45,7 +48,10 @@ struct DecodeTables {
     uint32_t first[MAX_LEN + 2];      // first codeword of each length (canonical)
     uint32_t count[MAX_LEN + 2];      // codewords of each length
     uint32_t base[MAX_LEN + 2];       // index in `symbols` of each length's first symbol
-    uint32_t lut[1 << LUT_BITS];      // (symbol << 8) | length for codewords of <= LUT_BITS bits; 0 = longer
+    // The whole codewords (up to 3) that the next LUT_BITS bits hold: bits 0-15, 16-31,
+    // 32-47 the symbols, 48-51 / 52-55 / 56-59 the bits consumed after 1 / 2 / 3 of
+    // them, 60-61 their number (0: the first codeword is longer than LUT_BITS).
+    unsigned long long lut[1 << LUT_BITS];
     int max_len;
 };
 // followed by uint16_t symbols[2R] in canonical order
@@ -270,8 +276,8 @@ __global__ void __launch_bounds__(TAB_THREADS) k_huff_tables(const uint8_t *__re
     __shared__ uint32_t wcnt[NW][NL];  // per warp: symbols of each length, then their offset in the length's run
     __shared__ int maxl_s;
     __shared__ unsigned int bad_s;
+    __shared__ uint32_t lut1[1 << LUT_BITS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < (1 << LUT_BITS); i += TAB_THREADS) t->lut[i] = 0u;
     if (tid < NL) {
         cnt_s[tid] = 0u;
         run_s[tid] = 0u;
@@ -334,11 +340,31 @@ __global__ void __launch_bounds__(TAB_THREADS) k_huff_tables(const uint8_t *__re
         }
         __syncthreads();
     }
+    // one-codeword table (symbol << 8 | length, 0 = longer than LUT_BITS), then the
+    // entries with every whole codeword of the LUT_BITS-bit window
+    for (int i = tid; i < (1 << LUT_BITS); i += TAB_THREADS) lut1[i] = 0u;
+    __syncthreads();
     for (int s = tid; s < nsym; s += TAB_THREADS) {
         const int l = lengths[s];
         if (!l || l > LUT_BITS) continue;
         const uint32_t lo = codewords[s] << (LUT_BITS - l), hi = lo + (1u << (LUT_BITS - l));
-        for (uint32_t v = lo; v < hi && v < (1u << LUT_BITS); ++v) t->lut[v] = ((uint32_t)s << 8) | (uint32_t)l;
+        for (uint32_t v = lo; v < hi && v < (1u << LUT_BITS); ++v) lut1[v] = ((uint32_t)s << 8) | (uint32_t)l;
+    }
+    __syncthreads();
+    constexpr uint32_t MASK = (1u << LUT_BITS) - 1u;
+    for (int v = tid; v < (1 << LUT_BITS); v += TAB_THREADS) {
+        unsigned long long e = 0;
+        uint32_t used = 0;
+        int n = 0;
+        for (; n < 3; ++n) {
+            const uint32_t e1 = lut1[((uint32_t)v << used) & MASK];  // bits past the window read as 0
+            const uint32_t l = e1 & 0xffu;
+            if (!e1 || used + l > (uint32_t)LUT_BITS) break;  // not a whole codeword of the window
+            used += l;
+            e |= (unsigned long long)(e1 >> 8) << (16 * n);
+            e |= (unsigned long long)used << (48 + 4 * n);
+        }
+        t->lut[v] = e | ((unsigned long long)n << 60);
     }
 }
 
@@ -352,7 +378,7 @@ __global__ void __launch_bounds__(DEC_THREADS) k_huff_decode(const uint32_t *__r
 {
     __shared__ DecodeTables t;
     __shared__ uint32_t stage[DEC_THREADS * (DEC_ROUND / 2 + 1)];  // a row of DEC_ROUND codes per thread, padded
-    extern __shared__ uint16_t sym_s[];                             // the symbol list when it fits (nsym_smem)
+    extern __shared__ uint16_t sym_s[];  // the symbol list when it fits (nsym_smem)
     {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(tg);
         uint32_t *dst = reinterpret_cast<uint32_t *>(&t);
@@ -377,25 +403,36 @@ __global__ void __launch_bounds__(DEC_THREADS) k_huff_decode(const uint32_t *__r
     // loaded one refill ahead of its use
     unsigned long long win = ((unsigned long long)(nw > 0 ? w[0] : 0u) << 32) | (nw > 1 ? w[1] : 0u);
     uint32_t ahead = nw > 2 ? w[2] : 0u;
-    uint32_t next = 3;    // next word to load
+    uint32_t next = 3;    // next word to take
     int avail = 64;       // valid bits in win (beyond the chunk's words they are zeros)
     const int cnt = live ? (int)min((unsigned long long)HCHUNK, n - chunk * HCHUNK) : 0;
     const int maxl = t.max_len;
     bool ok = true;
     uint16_t *row = reinterpret_cast<uint16_t *>(stage + threadIdx.x * RW);
     const uint32_t *wrows = stage + (threadIdx.x - lane) * RW;
+    // the warp's 32 chunks all hold HCHUNK codes and the codes are 4-byte aligned: the
+    // store phase needs no checks; each lane stores the words 2*(lane&15), +1 of row
+    // r + (lane >> 4) through a running pointer
+    const bool fast_store = vec && (chunk0 + 32) * HCHUNK <= n;
+    uint32_t *store_base = reinterpret_cast<uint32_t *>(codes + (chunk0 + (lane >> 4)) * HCHUNK) + (lane & 15);
     for (int j0 = 0; j0 < HCHUNK; j0 += DEC_ROUND) {
         const int jn = ok ? min(DEC_ROUND, cnt - j0) : 0;
-        for (int j = 0; j < jn; ++j) {
+        int j = 0;
+        while (j < jn) {
             const uint32_t top = (uint32_t)(win >> 32);
-            const uint32_t e = t.lut[top >> (32 - LUT_BITS)];
-            uint32_t sym, len;
-            if (e) {
-                sym = e >> 8;
-                len = e & 0xffu;
+            const unsigned long long e = t.lut[top >> (32 - LUT_BITS)];
+            const int ne = (int)(e >> 60);
+            uint32_t len;
+            if (ne) {  // up to three whole codewords; take what the round still needs
+                const int take = min(ne, jn - j);
+                row[j] = (uint16_t)e;
+                if (take > 1) row[j + 1] = (uint16_t)(e >> 16);
+                if (take > 2) row[j + 2] = (uint16_t)(e >> 32);
+                len = (uint32_t)(e >> (48 + 4 * (take - 1))) & 0xfu;
+                j += take;
             } else {  // longer codeword: the canonical rule, length by length
                 len = 0;
-                sym = 0;
+                uint32_t sym = 0;
                 for (int l = LUT_BITS + 1; l <= maxl; ++l) {
                     const uint32_t v = top >> (32 - l);
                     if (t.count[l] && v >= t.first[l] && v - t.first[l] < t.count[l]) {
@@ -409,8 +446,8 @@ __global__ void __launch_bounds__(DEC_THREADS) k_huff_decode(const uint32_t *__r
                     ok = false;
                     break;
                 }
+                row[j++] = (uint16_t)sym;
             }
-            row[j] = (uint16_t)sym;
             win <<= len;
             avail -= (int)len;
             if (avail <= 32) {  // refill the low 32 bits
@@ -423,20 +460,27 @@ __global__ void __launch_bounds__(DEC_THREADS) k_huff_decode(const uint32_t *__r
         __syncwarp();
         // the warp stores its 32 rows of this round, two rows (2 x DEC_ROUND codes) per instruction
         static_assert(DEC_ROUND == 32, "two staged rows per warp store");
-        for (int r = 0; r < 32; r += 2) {
-            const int rr = r + (lane >> 4), e = 2 * (lane & 15);
-            const unsigned long long c = chunk0 + rr;
-            if (c >= nchunks) break;
-            const long long m = min((long long)DEC_ROUND,
-                                    (long long)min((unsigned long long)HCHUNK, n - c * HCHUNK) - j0);  // codes to store
-            if (m <= 0) continue;
-            uint16_t *dst = codes + c * HCHUNK + j0;
-            const uint32_t v = wrows[rr * RW + (lane & 15)];
-            if (vec && e + 1 < m) {
-                *reinterpret_cast<uint32_t *>(dst + e) = v;
-            } else {
-                if (e < m) dst[e] = (uint16_t)(v & 0xffffu);
-                if (e + 1 < m) dst[e + 1] = (uint16_t)(v >> 16);
+        if (fast_store) {  // 32 whole chunks, 4-byte aligned codes: no checks, running pointers
+            uint32_t *dst = store_base + (j0 >> 1);
+            const uint32_t *src = wrows + (lane >> 4) * RW + (lane & 15);
+#pragma unroll 4
+            for (int r = 0; r < 32; r += 2) dst[(size_t)r * (HCHUNK / 2)] = src[r * RW];
+        } else {
+            for (int r = 0; r < 32; r += 2) {
+                const int rr = r + (lane >> 4), e = 2 * (lane & 15);
+                const unsigned long long c = chunk0 + rr;
+                if (c >= nchunks) break;
+                const long long m = min((long long)DEC_ROUND,
+                                        (long long)min((unsigned long long)HCHUNK, n - c * HCHUNK) - j0);  // codes to store
+                if (m <= 0) continue;
+                uint16_t *dst = codes + c * HCHUNK + j0;
+                const uint32_t v = wrows[rr * RW + (lane & 15)];
+                if (vec && e + 1 < m) {
+                    *reinterpret_cast<uint32_t *>(dst + e) = v;
+                } else {
+                    if (e < m) dst[e] = (uint16_t)(v & 0xffffu);
+                    if (e + 1 < m) dst[e + 1] = (uint16_t)(v >> 16);
+                }
             }
         }
         __syncwarp();
@@ -599,7 +643,8 @@ cudaError_t launch_huffman_decode(const uint32_t *words, const uint32_t *offsets
     if (nch == 0) return cudaSuccess;
     const bool vec = (reinterpret_cast<uintptr_t>(codes) & 3u) == 0;
     const int nsym_smem = nsym <= SYM_SMEM ? nsym : 0;
-    k_huff_decode<<<(unsigned)((nch + DEC_THREADS - 1) / DEC_THREADS), DEC_THREADS, 2 * (size_t)nsym_smem, s>>>(
+    const size_t dyn = 2 * (size_t)nsym_smem;
+    k_huff_decode<<<(unsigned)((nch + DEC_THREADS - 1) / DEC_THREADS), DEC_THREADS, dyn, s>>>(
         words, offsets, n, t, symbols, nsym_smem, codes, nch, vec, bad);
     return cudaGetLastError();
 }

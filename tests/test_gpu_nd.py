@@ -89,3 +89,42 @@ def test_nd_rejects_x_domain_and_batched():
                      device=x.device)
     it = G.compress_item(x, 1e-3, G.Config(ndim=2), bufs, ws)
     assert G.interp_compress_batched([it], None) == G.INTERP_EINVAL
+
+
+@pytest.mark.parametrize("ndim", [2, 1])
+def test_nd_fullsize_slices_match_oracle(ndim):
+    """The benchmark's 512 MiB 1-D / 2-D fields in the launch configuration it times
+    (autotuned, rel 1e-3): slices (2-D) and rows (1-D) are compressed independently,
+    so whole sampled slices / rows are compared with the oracle run on them alone,
+    bit for bit; everywhere else the error bound and the outlier/histogram counts."""
+    import oracle as O
+    shape = (32, 2048, 2048) if ndim == 2 else (64, 1, 1 << 21)
+    x = fields.grf(shape, 3.0, 5, device="cuda", fft_dtype=torch.float32)
+    torch.cuda.empty_cache()
+    cfg = G.Config(autotune=True, ndim=ndim)
+    cf = G.compress(x, 1e-3, cfg, capacity=x.numel() // 16)
+    xr = G.decompress(cf)
+    torch.cuda.synchronize()
+    h = cf.host_header(refresh=True)
+    assert h.status == 0
+    assert float((xr - x).abs().max()) <= float(np.float32(h.e[0]))
+    hist = cf.hist.cpu().numpy().view(np.uint32)
+    assert int(hist.sum()) == x.numel() and int(hist[0]) == int(h.n_outliers)
+    # the whole-field bound and configuration the GPU derived, used for every member
+    xh = x.cpu().numpy()
+    ocfg = O.autotune(xh, 512, ndim=ndim)
+    assert (tuple(h.cfg.dim_order), tuple(h.cfg.level_kind), tuple(h.cfg.cubic_kind)) == \
+        (ocfg.order, ocfg.level_kind, ocfg.cubic_kind)
+    eb_abs, e, twoe, inv2e = O.bounds_for(xh, 1e-3, "rel", ndim=ndim)
+    assert h.eb_abs == eb_abs
+    del xh
+    codes = cf.codes.view(shape)
+    A = 16 if ndim == 2 else 512
+    for z in (0, 17, 31) if ndim == 2 else (0, 40, 63):
+        xm = x[z:z + 1].cpu().numpy()
+        oc = O.compress(xm, ocfg, e, twoe, inv2e, eb_abs)
+        got = codes[z:z + 1].cpu().numpy().view(np.uint16)
+        assert np.array_equal(got, oc.codes), f"member {z}"
+        assert np.array_equal(xr[z:z + 1].cpu().numpy().view(np.uint32), oc.xrec.view(np.uint32))
+        anc = x[z, ::A, ::A] if ndim == 2 else x[z, :, ::A]
+        assert np.array_equal(oc.anchors, anc.cpu().numpy().reshape(-1))

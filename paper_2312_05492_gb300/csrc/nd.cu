@@ -28,7 +28,10 @@ namespace {
 constexpr int ND_THREADS = 256;
 constexpr int ND_MAX_LEVELS = 9;
 constexpr int ND_HIST_SMEM_BINS = 8192;
-constexpr int ND_CTAS_PER_SM = 6;  // persistent CTAs per SM (registers capped to fit them)
+// persistent CTAs per SM, registers capped at 40 to fit them (5 CTAs with 48 registers
+// were slower for the 2-D kernels)
+template <int NDIM>
+constexpr int nd_ctas_per_sm() { return 6; }
 
 template <int NDIM>
 struct NdGeom;
@@ -287,6 +290,173 @@ __device__ __forceinline__ void nd_full_pass(float *v, const NdPointCtx &c)
     }
 }
 
+// Stage a box clipped by the field's far end ((ey + 1) x (ex + 1) elements) with
+// every thread's loads issued before any is stored.
+template <int NDIM, typename T>
+__device__ __forceinline__ void nd_stage_clipped(T *dst, const T *src, long long row0, int nx, int x0, int ey,
+                                                 int ex)
+{
+    using G = NdGeom<NDIM>;
+    constexpr int K = (G::BY * G::BX + ND_THREADS - 1) / ND_THREADS;
+    const int w = ex + 1, ne = (ey + 1) * w;
+    T r[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = threadIdx.x + k * ND_THREADS;
+        if (e < ne) {
+            const int by = e / w, bx = e - by * w;
+            r[k] = __ldg(src + (row0 + by) * nx + x0 + bx);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int e = threadIdx.x + k * ND_THREADS;
+        if (e < ne) {
+            const int by = e / w, bx = e - by * w;
+            const int j = by * G::PX + bx;
+            dst[sizeof(T) == 4 ? vix<NDIM>(j) : hix<NDIM>(j)] = r[k];
+        }
+    }
+}
+
+// 2-D tiles clipped by the field's far end: chunk segments as for whole tiles, each
+// chunk line ending at min(lo + 16, the last staged index) and every point's stencil
+// by the neighbour-count rule (Sec. IV-B.1).
+template <int S, int AX, bool COMPRESS>
+__device__ __forceinline__ void nd2_seg_pass_clipped(float *v, const NdPointCtx &c, int so, int ea, int eo)
+{
+    using G = NdGeom<2>;
+    constexpr int SA = AX == 1 ? G::PX : 1;
+    constexpr int SOM = AX == 1 ? 1 : G::PX;
+    constexpr int NKMAX = 16 / (2 * S) + 1;
+    const int no = eo / so + 1;
+    const int nch = ea > 0 ? (ea - 1) / G::A + 1 : 0;  // chunks holding points to predict
+#pragma unroll 1
+    for (int w = threadIdx.x; w < no * nch; w += ND_THREADS) {
+        const int io = w % no, ch = w / no;
+        const int m = io * so, n0 = ch * G::A;
+        const int hl = min(G::A, ea - n0);  // last offset of the (possibly truncated) chunk line
+        float *line = v + m * SOM + n0 * SA;
+        float k[NKMAX];
+#pragma unroll
+        for (int q = 0; q < NKMAX; ++q) k[q] = (2 * q * S <= hl) ? line[q * 2 * S * SA] : 0.0f;
+#pragma unroll
+        for (int q = 0; q + 1 < NKMAX; ++q) {
+            const int o = (2 * q + 1) * S;
+            if (o > hl) break;
+            float p;
+            if (o + S > hl) {
+                p = k[q];  // one neighbour: copy of x_{n-s}
+            } else if (!c.spline) {
+                p = sp_linear(k[q], k[q + 1]);
+            } else {
+                const bool hm3 = q >= 1, hp3 = o + 3 * S <= hl;
+                const float m3 = k[q > 0 ? q - 1 : 0], p3 = k[q + 2 < NKMAX ? q + 2 : q];
+                if (hm3 && hp3) p = sp_cubic(c.ck, m3, k[q], k[q + 1], p3);
+                else if (hm3) p = sp_quad_left(m3, k[q], k[q + 1]);
+                else if (hp3) p = sp_quad_right(k[q], k[q + 1], p3);
+                else p = sp_linear(k[q], k[q + 1]);
+            }
+            const int by = AX == 1 ? n0 + o : m, bx = AX == 2 ? n0 + o : m;
+            if (COMPRESS) {
+                float xr;
+                const uint32_t code = quantize(line[o * SA], p, c.q, c.cbias, c.Rf, xr);
+                line[o * SA] = xr;
+                if (by < G::TY && bx < G::TX) c.cs[by * G::TX + bx] = (uint16_t)code;
+            } else {
+                const uint32_t code = c.cb[by * G::PX + bx];
+                line[o * SA] = code ? p + code_to_q(code, c.cbias) * c.q.twoe
+                                    : c.xrec[(c.row0 + by) * c.nx + c.x0 + bx];
+            }
+        }
+    }
+}
+
+template <int S, bool XFIRST, bool COMPRESS>
+__device__ __forceinline__ void nd2_levels_clipped(float *v, NdPointCtx &c, const LevelQ *lq, const NdCfg &cfg,
+                                                   int ey, int ex)
+{
+    constexpr int l = S >= 8 ? 3 : S >= 4 ? 2 : S >= 2 ? 1 : 0;
+    c.q = lq[l];
+    c.spline = cfg.level_kind[l < 2 ? l : 2];
+    constexpr int F = XFIRST ? 2 : 1, O = XFIRST ? 1 : 2;
+    c.ck = cubic_coeffs(cfg.cubic_kind[F]);
+    nd2_seg_pass_clipped<S, F, COMPRESS>(v, c, 2 * S, F == 2 ? ex : ey, F == 2 ? ey : ex);
+    __syncthreads();
+    c.ck = cubic_coeffs(cfg.cubic_kind[O]);
+    nd2_seg_pass_clipped<S, O, COMPRESS>(v, c, S, O == 2 ? ex : ey, O == 2 ? ey : ex);
+    __syncthreads();
+    if constexpr (S > 1) nd2_levels_clipped<S / 2, XFIRST, COMPRESS>(v, c, lq, cfg, ey, ex);
+}
+
+template <bool COMPRESS>
+__device__ __forceinline__ void nd2_clipped_tile(float *v, NdPointCtx &c, const LevelQ *lq, const NdCfg &cfg,
+                                                 int ey, int ex)
+{
+    int px = 0, py = 0;
+    for (int j = 0; j < 3; ++j) {
+        if (cfg.order[j] == 2) px = j;
+        if (cfg.order[j] == 1) py = j;
+    }
+    if (py < px)
+        nd2_levels_clipped<NdGeom<2>::A / 2, false, COMPRESS>(v, c, lq, cfg, ey, ex);
+    else
+        nd2_levels_clipped<NdGeom<2>::A / 2, true, COMPRESS>(v, c, lq, cfg, ey, ex);
+}
+
+// 2-D whole tiles, chunk segments: one work unit is the line of one 16-point chunk
+// along the pass axis (its 17 points, the chunk's closing point included); the
+// known points (even multiples of s) are loaded once and give all the chunk line's
+// predictions from registers, with the stencils of whole chunks (Fig. 3 at twice the
+// scale: the first point right-quadratic, the last left-quadratic, the rest cubic;
+// a lone midpoint linear).
+template <int S, int AX, int SO, bool COMPRESS>
+__device__ __forceinline__ void nd2_seg_pass(float *v, const NdPointCtx &c)
+{
+    using G = NdGeom<2>;
+    constexpr int NO = (AX == 2 ? G::BY - 1 : G::BX - 1) / SO + 1;  // lines along the other axis
+    constexpr int NCH = AX == 2 ? G::TX / G::A : 1;                 // chunks along the axis
+    constexpr int SA = AX == 1 ? G::PX : 1;
+    constexpr int SOM = AX == 1 ? 1 : G::PX;
+    constexpr int NK = 16 / (2 * S) + 1;  // known points of a chunk line
+#pragma unroll 1
+    for (int w = threadIdx.x; w < NO * NCH; w += ND_THREADS) {
+        const int io = w % NO, ch = w / NO;  // consecutive threads take consecutive lines
+        const int m = io * SO, n0 = ch * G::A;
+        float *line = v + m * SOM + n0 * SA;
+        float k[NK];
+#pragma unroll
+        for (int q = 0; q < NK; ++q) k[q] = line[q * 2 * S * SA];
+        auto emit = [&](int q, float p) {  // prediction of the point between k[q] and k[q + 1]
+            const int o = (2 * q + 1) * S;
+            const int by = AX == 1 ? n0 + o : m, bx = AX == 2 ? n0 + o : m;
+            if (COMPRESS) {
+                float xr;
+                const uint32_t code = quantize(line[o * SA], p, c.q, c.cbias, c.Rf, xr);
+                line[o * SA] = xr;
+                if (by < G::TY && bx < G::TX) c.cs[by * G::TX + bx] = (uint16_t)code;
+            } else {
+                const uint32_t code = c.cb[(by * G::PX + bx)];
+                line[o * SA] = code ? p + code_to_q(code, c.cbias) * c.q.twoe
+                                    : c.xrec[(c.row0 + by) * c.nx + c.x0 + bx];
+            }
+        };
+        if (!c.spline || NK == 2) {
+#pragma unroll
+            for (int q = 0; q + 1 < NK; ++q) emit(q, sp_linear(k[q], k[q + 1]));
+        } else {
+#pragma unroll
+            for (int q = 0; q + 1 < NK; ++q) {
+                float p;
+                if (q == 0) p = sp_quad_right(k[0], k[1], k[2]);
+                else if (q == NK - 2) p = sp_quad_left(k[NK - 3], k[NK - 2], k[NK - 1]);
+                else p = sp_cubic(c.ck, k[q - 1], k[q], k[q + 1], k[q + 2]);
+                emit(q, p);
+            }
+        }
+    }
+}
+
 // Levels S, S/2, ..., 1 of a full tile; in 2-D the axis interpolated first in a level
 // sees the other on the 2s-grid, the second on the s-grid.
 template <int NDIM, int S, bool XFIRST, bool COMPRESS>
@@ -303,10 +473,10 @@ __device__ __forceinline__ void nd_full_levels(float *v, NdPointCtx &c, const Le
     } else {
         constexpr int F = XFIRST ? 2 : 1, O = XFIRST ? 1 : 2;
         c.ck = cubic_coeffs(cfg.cubic_kind[F]);
-        nd_full_pass<NDIM, S, F, 2 * S, COMPRESS>(v, c);
+        nd2_seg_pass<S, F, 2 * S, COMPRESS>(v, c);
         __syncthreads();
         c.ck = cubic_coeffs(cfg.cubic_kind[O]);
-        nd_full_pass<NDIM, S, O, S, COMPRESS>(v, c);
+        nd2_seg_pass<S, O, S, COMPRESS>(v, c);
         __syncthreads();
     }
     if constexpr (S > 1) nd_full_levels<NDIM, S / 2, XFIRST, COMPRESS>(v, c, lq, cfg);
@@ -343,26 +513,21 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
 
     // stage the box
     const bool full = t.ey == G::BY - 1 && t.ex == G::BX - 1;
-    if (full) {
-        nd_stage_full<NDIM>(v, a.x, t.row0, d.nx, t.x0);
-    } else {
-        for (int by = 0; by <= t.ey; ++by) {
-            const float *src = a.x + (t.row0 + by) * d.nx + t.x0;
-            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) v[vix<NDIM>(by * G::PX + bx)] = __ldg(src + bx);
-        }
-    }
+    if (full) nd_stage_full<NDIM>(v, a.x, t.row0, d.nx, t.x0);
+    else nd_stage_clipped<NDIM>(v, a.x, t.row0, d.nx, t.x0, t.ey, t.ex);
     // owned anchors: code R, value kept
     for (int i = tid; i < hsize<NDIM>(G::TY * G::TX); i += ND_THREADS) cs[i] = (uint16_t)a.radius;
     __syncthreads();
 
-    if (full) {
+    if (full || NDIM == 2) {
         NdPointCtx c;
         c.cbias = cbias;
         c.Rf = Rf;
         c.cs = cs;
-        nd_full_tile<NDIM, true>(v, c, lq, cfg);
+        if (full) nd_full_tile<NDIM, true>(v, c, lq, cfg);
+        else nd2_clipped_tile<true>(v, c, lq, cfg, t.ey, t.ex);
     }
-    for (int l = full ? -1 : L - 1; l >= 0; --l) {
+    for (int l = (full || NDIM == 2) ? -1 : L - 1; l >= 0; --l) {
         const int s = 1 << l;
         const LevelQ q = lq[l];
         const int spline = cfg.level_kind[l < 2 ? l : 2];
@@ -430,7 +595,7 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(ND_THREADS, ND_CTAS_PER_SM) k_nd_compress(CompressArgs a)
+__global__ void __launch_bounds__(ND_THREADS, nd_ctas_per_sm<NDIM>()) k_nd_compress(CompressArgs a)
 {
     using G = NdGeom<NDIM>;
     __shared__ float v[vsize<NDIM>(G::BY * G::PX)];
@@ -476,11 +641,8 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
     const int ax = (d.nx - 1) / G::A + 1;
     const bool full = t.ey == G::BY - 1 && t.ex == G::BX - 1;
     if (full) nd_stage_full<NDIM>(cb, a.codes, t.row0, d.nx, t.x0);
+    else nd_stage_clipped<NDIM>(cb, a.codes, t.row0, d.nx, t.x0, t.ey, t.ex);
     for (int by = 0; by <= t.ey; ++by) {
-        if (!full) {
-            const uint16_t *src = a.codes + (t.row0 + by) * d.nx + t.x0;
-            for (int bx = tid; bx <= t.ex; bx += ND_THREADS) cb[hix<NDIM>(by * G::PX + bx)] = __ldg(src + bx);
-        }
         const bool anchor_row = NDIM == 1 || (t.y0 + by) % G::A == 0;
         if (anchor_row) {
             const long long arow =
@@ -491,7 +653,7 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
     }
     __syncthreads();
 
-    if (full) {
+    if (full || NDIM == 2) {
         NdPointCtx c;
         c.cbias = cbias;
         c.cb = cb;
@@ -499,9 +661,10 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
         c.row0 = t.row0;
         c.nx = d.nx;
         c.x0 = t.x0;
-        nd_full_tile<NDIM, false>(v, c, lq, cfg);
+        if (full) nd_full_tile<NDIM, false>(v, c, lq, cfg);
+        else nd2_clipped_tile<false>(v, c, lq, cfg, t.ey, t.ex);
     }
-    for (int l = full ? -1 : L - 1; l >= 0; --l) {
+    for (int l = (full || NDIM == 2) ? -1 : L - 1; l >= 0; --l) {
         const int s = 1 << l;
         const float twoe = lq[l].twoe;
         const int spline = cfg.level_kind[l < 2 ? l : 2];
@@ -542,7 +705,7 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(ND_THREADS, ND_CTAS_PER_SM) k_nd_decompress(DecompressArgs a)
+__global__ void __launch_bounds__(ND_THREADS, nd_ctas_per_sm<NDIM>()) k_nd_decompress(DecompressArgs a)
 {
     using G = NdGeom<NDIM>;
     __shared__ float v[vsize<NDIM>(G::BY * G::PX)];
@@ -574,7 +737,7 @@ cudaError_t launch_nd_compress(int ndim, const CompressArgs &a, cudaStream_t s)
     const int tiles = nd_tiles_host(ndim, a.dims);
     if (tiles == 0) return cudaSuccess;
     const size_t hist_smem = (a.hist && 2 * a.radius <= ND_HIST_SMEM_BINS) ? sizeof(uint32_t) * 2 * a.radius : 0;
-    const int grid = min(tiles, sm_count() * ND_CTAS_PER_SM);
+    const int grid = min(tiles, sm_count() * (ndim == 2 ? nd_ctas_per_sm<2>() : nd_ctas_per_sm<1>()));
     if (ndim == 2)
         k_nd_compress<2><<<grid, ND_THREADS, hist_smem, s>>>(a);
     else
@@ -587,7 +750,7 @@ cudaError_t launch_nd_decompress(int ndim, const DecompressArgs &a, cudaStream_t
     if (ndim != 1 && ndim != 2) return cudaErrorInvalidValue;
     const int tiles = nd_tiles_host(ndim, a.dims);
     if (tiles == 0) return cudaSuccess;
-    const int grid = min(tiles, sm_count() * ND_CTAS_PER_SM);
+    const int grid = min(tiles, sm_count() * (ndim == 2 ? nd_ctas_per_sm<2>() : nd_ctas_per_sm<1>()));
     if (ndim == 2)
         k_nd_decompress<2><<<grid, ND_THREADS, 0, s>>>(a);
     else

@@ -12,9 +12,12 @@
 // of one row.  Persistent CTAs take tiles in turn; a CTA stages the tile with its
 // closing row and column (the anchors and points its chunks borrow from the next
 // tile) in shared memory, runs every pass on it, and writes only what it owns.
-// Passes inside a tile are separated by barriers; tiles are independent.  The level
-// constants (double arithmetic, slow on this part) are formed once per CTA, one
-// thread per level.
+// Passes inside a tile are separated by barriers; tiles are independent.  2-D passes
+// work on chunk lines (the 17 points of one chunk along the pass axis, its known
+// points in registers); 1-D passes on points, with compile-time shapes for whole
+// tiles.  Tiles clipped by the field's end take the neighbour-count rule per point.
+// The level constants (double arithmetic, slow on this part) are formed once per
+// CTA, one thread per level.
 //
 // Outputs match the 3-D path's formats: codes (q + R, 0 for outliers, R at
 // anchors), anchors [nz'][ny'][nx'], the fused histogram, and the outlier bitmap

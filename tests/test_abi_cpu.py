@@ -93,3 +93,40 @@ def test_binding_refuses_cpu_tensors(G):
     import torch
     with pytest.raises(G.InterpError):
         G.compress(torch.zeros(8, 8, 8), 1e-3)
+
+
+def test_anchor_count_nd_matches_oracle(G):
+    import oracle as O
+    for dims in [(1, 17, 17), (3, 33, 40), (2, 3, 1025), (1, 1, 512), (5, 100, 7), (64, 1, 1 << 21)]:
+        for ndim in (1, 2, 3):
+            assert G.interp_anchor_count_nd(dims, ndim) == O.anchor_count(dims, ndim), (dims, ndim)
+    assert G.interp_anchor_count_nd((8, 8, 8), 0) == G.interp_anchor_count((8, 8, 8))
+    assert G.interp_anchor_count_nd((8, 8, 8), 4) == 0
+    assert G.interp_anchor_count_nd((0, 8, 8), 2) == 0
+
+
+@pytest.mark.parametrize("change", [dict(ndim=2, domain_x=32), dict(ndim=1, domain_x=32), dict(ndim=4),
+                                    dict(ndim=-1)])
+def test_nd_configuration_errors(G, change):
+    cfg = G.Config(**change).to_c()
+    assert G.interp_workspace_bytes((8, 8, 8), cfg) == 0
+    rc = G.interp_compress(1, (8, 8, 8), 1e-3, cfg, 1, 1, 1, 1, 16, None, 1, 1, 1 << 20, None)
+    assert rc == G.INTERP_EINVAL
+
+
+def test_decompress_nd_argument_errors(G):
+    # rejected on the host, before anything is enqueued
+    assert G.interp_decompress_nd(5, (8, 8, 8), 1, 1, 1, 1, 1, 16, 1, None) == G.INTERP_EINVAL
+    assert G.interp_decompress_nd(2, (0, 8, 8), 1, 1, 1, 1, 1, 16, 1, None) == G.INTERP_EINVAL
+    assert G.interp_decompress_nd(2, (8, 8, 8), None, 1, 1, 1, 1, 16, 1, None) == G.INTERP_EINVAL
+    assert G.interp_decompress_nd(1, (8, 8, 8), 1, 1, 1, None, None, 16, 1, None) == G.INTERP_EINVAL
+
+
+def test_huffman_sizes(G):
+    lib = G.load()
+    assert lib.interp_huffman_chunks(0) == 0 and lib.interp_huffman_chunks(1025) == 2
+    assert lib.interp_huffman_capacity_words(1024, 16) >= 1024 * 16 // 32
+    assert lib.interp_huffman_capacity_words(1024, 25) == 0
+    assert lib.interp_huffman_workspace_bytes(1 << 27, 512) > lib.interp_huffman_workspace_bytes(1024, 512) > 0
+    assert lib.interp_huffman_workspace_bytes(1024, 1) == 0
+    assert lib.interp_huffman_workspace_bytes(1 << 32, 512) == 0

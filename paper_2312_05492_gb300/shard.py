@@ -106,6 +106,9 @@ def compress(x_local, slab: Slab, dims, eps: float, cfg, backend, group=None, eb
     nz, ny, nx = (int(d) for d in dims)
     if getattr(cfg, "autotune", False):
         raise ValueError("a sharded field needs an explicit configuration (autotune looks at the whole field)")
+    if getattr(cfg, "ndim", 3) not in (0, 3):
+        raise ValueError("slabs split the 8^3-chunk geometry; 1-D and 2-D fields are independent per slice or "
+                         "row and are split by the caller")
     if not slab.empty and tuple(int(d) for d in x_local.shape) != (slab.zc - slab.z0, ny, nx):
         raise ValueError(f"rank {slab.rank}: sub-field shape {tuple(x_local.shape)} does not match {slab}")
     rng = backend.value_range(x_local) if not slab.empty else (float("inf"), float("-inf"))

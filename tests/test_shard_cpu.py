@@ -154,3 +154,11 @@ def test_sharded_equals_single_field(case):
     assert np.array_equal(xr_all.view(np.uint32), ref.xrec.view(np.uint32))
     if case == "split":
         assert ref.n_outliers > 0  # the outlier offsets were exercised
+
+
+def test_sharding_rejects_1d_2d_geometry():
+    from paper_2312_05492_gb300 import shard
+    sl = shard.slabs(64, 2)[0]
+    for ndim in (1, 2):
+        with pytest.raises(ValueError):
+            shard.compress(torch.zeros(sl.zc - sl.z0, 8, 8), sl, (64, 8, 8), 1e-3, O.Config(ndim=ndim), backend=None)

@@ -121,7 +121,9 @@ size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg);
  *   eb           error bound: absolute, or relative to (max - min) when cfg->eb_mode = 1
  *   cfg          host pointer to the configuration (copied; not retained)
  *   d_anchors    [interp_anchor_count(dims)] out: x at points with all coords = 0 mod 8,
- *                laid out [nz'][ny'][nx'] with n' = floor((n - 1)/8) + 1
+ *                laid out [nz'][ny'][nx'] with n' = floor((n - 1)/8) + 1 (for cfg->ndim
+ *                1 or 2: [interp_anchor_count_nd(dims, ndim)], the chunked coords = 0
+ *                mod 512 / 16, every index along the other axes)
  *   d_codes      [N] out: uint16 quant-codes; q + R for kept points, 0 for outliers,
  *                R at anchors
  *   d_out_idx,
@@ -132,9 +134,10 @@ size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg);
  *   d_hdr        out: device header (bounds, effective config, counts, status)
  *   d_ws         device scratch of ws_bytes >= interp_workspace_bytes(dims, cfg)
  * Guarantee: for every point |x - x'| <= e_l of its level, where x' is the output of
- * interp_decompress and e_l = float(eb_abs / alpha^l) (header e[l]); e_0, the largest,
- * is eb_abs rounded to float, so it may exceed eb_abs by up to half a float ulp.
- * Anchors and outliers are exact. */
+ * interp_decompress and e_l = float(eb_abs / alpha^l) (header e[l] for l <= 2); e_0, the
+ * largest, is eb_abs rounded to float, so it may exceed eb_abs by up to half a float ulp.
+ * Anchors and outliers are exact.  Fields compressed with cfg->ndim 1 or 2 are
+ * decompressed by interp_decompress_nd. */
 int interp_compress(const float *d_x, const int64_t dims[3], double eb, const interp_config *cfg,
                     float *d_anchors, uint16_t *d_codes, uint32_t *d_out_idx, float *d_out_val,
                     uint64_t out_capacity, uint32_t *d_hist, interp_header *d_hdr,

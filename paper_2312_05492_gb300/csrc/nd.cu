@@ -66,6 +66,16 @@ __host__ __device__ constexpr int vsize(int n) { return NDIM == 1 ? n + (n >> 5)
 template <int NDIM>
 __host__ __device__ constexpr int hsize(int n) { return NDIM == 1 ? n + ((n >> 6) << 1) + 2 : n; }
 
+// the 16 bits of x moved to the even bit positions (bit i -> bit 2i)
+__device__ __forceinline__ uint32_t spread16(uint32_t x)
+{
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
 struct NdTile {
     long long row0;  // first global (z, y) row of the tile: z * ny + y0
     int z, y0, x0;   // tile origin
@@ -572,10 +582,44 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
                 a.anchors[arow * ax + (t.x0 + bx) / G::A] = v[vix<NDIM>(bx)];
     }
 
-    // codes, outlier bitmap words and the histogram of the owned points, one
-    // 32-column strip of a row per warp step
+    // codes, outlier bitmap words and the histogram of the owned points
     const int lane = tid & 31, warp = tid >> 5;
     const int wpr = (d.nx + 31) / 32;
+    const bool pairs = NDIM == 2 && t.ox == G::TX && (d.nx & 1) == 0 &&
+                       (reinterpret_cast<uintptr_t>(a.codes) & 3u) == 0;
+    if (pairs) {
+        // 2-D tiles owning all 128 columns: a warp step takes 64 codes of a row, two per
+        // lane (4-byte loads and stores); the two 32-column words interleave the ballots
+        // of the pairs' low and high codes
+        const uint32_t *cs2 = reinterpret_cast<const uint32_t *>(cs);
+        for (int u = warp; u < t.oy * 2; u += ND_THREADS / 32) {
+            const int by = u >> 1, half = u & 1;
+            const int c0 = half * 64 + 2 * lane;
+            const uint32_t w = cs2[(by * G::TX + c0) >> 1];
+            const uint32_t lo = w & 0xffffu, hi = w >> 16;
+            const long long row = t.row0 + by;
+            *reinterpret_cast<uint32_t *>(a.codes + row * d.nx + t.x0 + c0) = w;
+            const uint32_t zl = __ballot_sync(0xffffffffu, lo == 0u), zh = __ballot_sync(0xffffffffu, hi == 0u);
+            if (lane == 0) {
+                const long long gw = row * wpr + (t.x0 >> 5) + 2 * half;  // row-major bitmap
+                const uint32_t w0 = spread16(zl & 0xffffu) | (spread16(zh & 0xffffu) << 1);
+                const uint32_t w1 = spread16(zl >> 16) | (spread16(zh >> 16) << 1);
+                a.bitmap[gw] = w0;
+                a.bitmap[gw + 1] = w1;
+                if (w0) atomicAdd(a.blockcnt + gw / BITMAP_BLOCK_WORDS, (uint32_t)__popc(w0));
+                if (w1) atomicAdd(a.blockcnt + (gw + 1) / BITMAP_BLOCK_WORDS, (uint32_t)__popc(w1));
+            }
+            if (a.hist) {
+                if (lo == (uint32_t)a.radius) ++central;
+                else if (lo < (uint32_t)bins) atomicAdd(smem_hist ? &hs[lo] : &a.hist[lo], 1u);
+                if (hi == (uint32_t)a.radius) ++central;
+                else if (hi < (uint32_t)bins) atomicAdd(smem_hist ? &hs[hi] : &a.hist[hi], 1u);
+            }
+        }
+        __syncthreads();  // the box and the code stage are reused by the next tile
+        return;
+    }
+    // one 32-column strip of a row per warp step
     const int strips = (t.ox + 31) / 32;
     for (int u = warp; u < t.oy * strips; u += ND_THREADS / 32) {
         const int by = u / strips, strip = u - by * strips, bx = strip * 32 + lane;
@@ -602,7 +646,7 @@ __global__ void __launch_bounds__(ND_THREADS, nd_ctas_per_sm<NDIM>()) k_nd_compr
 {
     using G = NdGeom<NDIM>;
     __shared__ float v[vsize<NDIM>(G::BY * G::PX)];
-    __shared__ uint16_t cs[hsize<NDIM>(G::TY * G::TX)];
+    __shared__ __align__(16) uint16_t cs[hsize<NDIM>(G::TY * G::TX)];
     __shared__ LevelQ lq[ND_MAX_LEVELS];
     extern __shared__ uint32_t hs[];  // histogram bins when 2R <= ND_HIST_SMEM_BINS
     const int tid = threadIdx.x;

@@ -37,10 +37,10 @@ constexpr int EZ = 9, EY = OY + 1, EX = OX + 1;  // slab box extents (z, y, x)
 constexpr int PLANE = EY * EX;                   // 561 floats, odd: conflict-free row walks
 constexpr int BOXF = EZ * PLANE;                 // floats per slab box
 constexpr int CP = OX + 2;                       // u16 pitch of code rows (17 words, odd)
-constexpr int STAGE_PLANE = OY * CP;             // compression code staging: owned rows only
-constexpr int STAGE = EZ * STAGE_PLANE;
-constexpr int CBOX_PLANE = EY * CP;              // decompression code box: all rows
-constexpr int CBOX = EZ * CBOX_PLANE;
+constexpr int CBOX_PLANE = EY * CP;              // code box (compression staging, decompression input):
+constexpr int CBOX = EZ * CBOX_PLANE;            // every row and column of the slab box
+constexpr int STAGE_PLANE = CBOX_PLANE;
+constexpr int STAGE = CBOX;
 // TMA landing buffers: dense boxes whose rows are a multiple of 16 bytes
 constexpr int XP = 36;                           // floats per landed row (x 0..35)
 constexpr int XPL = 8;                           // landed input planes: 1..8 of a slab (plane 0 is
@@ -129,6 +129,7 @@ struct Levels {
     uint32_t cbias;  // kMagicBits - R
     int xdom32;      // neighbour domain along x: the column's 32-point block (else the chunk)
     int nseg[2][3][3];  // segments of pass k of level l, [plane 0 carried][l][k]
+    int ord_id;         // index of the axis order (ord_axis)
 };
 
 __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
@@ -142,6 +143,7 @@ __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
         lv.order[l] = h->cfg.dim_order[l];
     }
     for (int k = 0; k < 3; ++k) lv.rank[lv.order[k]] = k;
+    lv.ord_id = 2 * lv.order[0] + (lv.order[1] > lv.order[2] ? 1 : 0);
     lv.R = h->cfg.radius;
     lv.Rf = (float)lv.R;
     lv.cbias = kMagicBits - (uint32_t)lv.R;
@@ -364,6 +366,207 @@ __device__ __forceinline__ void run_levels(float *box, const Sink &sk, const Sla
     }
 }
 
+
+// ------------------------------------------------------------ passes with fixed geometry
+// The default neighbour domain (the closed 8^3 chunk) with the axis order fixed at
+// compile time: every pass's segment count, strides and line offsets are
+// constants, so a thread decodes its segments with constant divisions and the
+// loops unroll.  One instantiation per axis order (six) and per state of plane 0
+// (carried or not); the kernel selects it once per slab.
+//
+// Axis orders are indexed 2*o0 + (o1 > o2): 012, 021, 102, 120, 201, 210.
+__host__ __device__ constexpr int ord_axis(int ord, int k)
+{
+    // o0 = ord / 2; the two others in ascending order are (a, b); bit 0 swaps them
+    return k == 0 ? ord / 2
+                  : ((k == 1) == ((ord & 1) == 0) ? (ord / 2 == 0 ? 1 : 0) : (ord / 2 == 2 ? 1 : 2));
+}
+__host__ __device__ constexpr int ord_rank(int ord, int axis)
+{
+    return ord_axis(ord, 0) == axis ? 0 : (ord_axis(ord, 1) == axis ? 1 : 2);
+}
+static_assert(ord_axis(0, 1) == 1 && ord_axis(0, 2) == 2 && ord_axis(1, 1) == 2 && ord_axis(1, 2) == 1 &&
+                  ord_axis(2, 0) == 1 && ord_axis(2, 1) == 0 && ord_axis(2, 2) == 2 && ord_axis(3, 1) == 2 &&
+                  ord_axis(3, 2) == 0 && ord_axis(4, 1) == 0 && ord_axis(4, 2) == 1 && ord_axis(5, 1) == 1 &&
+                  ord_axis(5, 2) == 0,
+              "axis orders");
+
+// Per-slab values of the fixed-geometry passes.
+struct FastCtx {
+    float *box;
+    uint16_t *codes;  // code box: compression staging or decompression input (same layout)
+    int nfull[3];     // chunks along each axis that end inside the field (full chunks)
+    int rem[3];       // last in-field offset along each axis, from the box origin
+};
+
+// One point of a segment: compression quantizes and stages the code (the value
+// stays in the box unless no later pass or slab reads it); decompression applies
+// the stored code (code 0 = outlier, whose stored value is already in the box).
+template <bool COMPRESS>
+__device__ __forceinline__ void seg_emit(float *L, uint16_t *C, int ob, int oc, float p, const LevelQ &Lq,
+                                         uint32_t cbias, float Rf, bool keep)
+{
+    if (COMPRESS) {
+        float xr;
+        const uint32_t code = quantize(L[ob], p, Lq, cbias, Rf, xr);
+        if (keep) L[ob] = xr;
+        C[oc] = (uint16_t)code;
+    } else {
+        const uint32_t code = C[oc];
+        const float xq = p + code_to_q(code, cbias) * Lq.twoe;
+        if (code) L[ob] = xq;
+    }
+}
+
+// A segment of a full chunk: the fixed stencils of Fig. 3 (SPLINE: cubic at
+// offsets 3 and 5, quadratics at 1 and 7 for stride 1; quadratics at stride 2;
+// stride 4 is always linear).
+template <bool COMPRESS, int S, int BD, int KD, bool SPLINE>
+__device__ __forceinline__ void seg_full(float *L, uint16_t *C, const LevelQ &Lq, const Cubic &cub, uint32_t cbias,
+                                         float Rf, bool keep)
+{
+    if (S == 4) {
+        seg_emit<COMPRESS>(L, C, 4 * BD, 4 * KD, sp_linear(L[0], L[8 * BD]), Lq, cbias, Rf, keep);
+    } else if (S == 2) {
+        const float k0 = L[0], k4 = L[4 * BD], k8 = L[8 * BD];
+        seg_emit<COMPRESS>(L, C, 2 * BD, 2 * KD, SPLINE ? sp_quad_right(k0, k4, k8) : sp_linear(k0, k4), Lq, cbias,
+                           Rf, keep);
+        seg_emit<COMPRESS>(L, C, 6 * BD, 6 * KD, SPLINE ? sp_quad_left(k0, k4, k8) : sp_linear(k4, k8), Lq, cbias,
+                           Rf, keep);
+    } else {
+        const float k0 = L[0], k2 = L[2 * BD], k4 = L[4 * BD], k6 = L[6 * BD], k8 = L[8 * BD];
+        seg_emit<COMPRESS>(L, C, BD, KD, SPLINE ? sp_quad_right(k0, k2, k4) : sp_linear(k0, k2), Lq, cbias, Rf,
+                           keep);
+        seg_emit<COMPRESS>(L, C, 3 * BD, 3 * KD, SPLINE ? sp_cubic(cub, k0, k2, k4, k6) : sp_linear(k2, k4), Lq,
+                           cbias, Rf, keep);
+        seg_emit<COMPRESS>(L, C, 5 * BD, 5 * KD, SPLINE ? sp_cubic(cub, k2, k4, k6, k8) : sp_linear(k4, k6), Lq,
+                           cbias, Rf, keep);
+        seg_emit<COMPRESS>(L, C, 7 * BD, 7 * KD, SPLINE ? sp_quad_left(k4, k6, k8) : sp_linear(k6, k8), Lq, cbias,
+                           Rf, keep);
+    }
+}
+
+// A segment of a chunk cut by the field's far edge (last in-field offset hi < 8):
+// the neighbour-count rule point by point (Sec. IV-B.1).
+template <bool COMPRESS, int S, int BD, int KD>
+__device__ __forceinline__ void seg_trunc(float *L, uint16_t *C, int hi, bool spline, const LevelQ &Lq,
+                                          const Cubic &cub, uint32_t cbias, float Rf, bool keep)
+{
+#pragma unroll
+    for (int o = S; o < 8; o += 2 * S) {
+        if (o > hi) break;
+        const bool has_m3 = o - 3 * S >= 0;
+        const bool has_p1 = o + S <= hi;
+        const bool has_p3 = o + 3 * S <= hi;
+        const float m1 = L[(o - S) * BD];
+        float p;
+        if (!has_p1) {
+            p = m1;
+        } else {
+            const float p1 = L[(o + S) * BD];
+            if (!spline) p = sp_linear(m1, p1);
+            else if (has_m3 && has_p3) p = sp_cubic(cub, L[(o - 3 * S) * BD], m1, p1, L[(o + 3 * S) * BD]);
+            else if (has_m3) p = sp_quad_left(L[(o - 3 * S) * BD], m1, p1);
+            else if (has_p3) p = sp_quad_right(m1, p1, L[(o + 3 * S) * BD]);
+            else p = sp_linear(m1, p1);
+        }
+        seg_emit<COMPRESS>(L, C, o * BD, o * KD, p, Lq, cbias, Rf, keep);
+    }
+}
+
+// Pass k of the level of stride S for axis order ORD.  Segments are numbered with
+// U (the faster other axis) fastest, then V, then the chunk along D; thread t
+// takes segments t, t + NT, ...
+template <bool COMPRESS, int ORD, bool CARRIED, int S, int K, bool SPLINE>
+__device__ __forceinline__ void fast_pass(const FastCtx &c, const LevelQ &Lq, const Cubic &cub, uint32_t cbias,
+                                          float Rf)
+{
+    constexpr int D = ord_axis(ORD, K);
+    constexpr int U = axis_u(D), V = axis_v(D);
+    constexpr int stepU = ord_rank(ORD, U) < K ? S : 2 * S;
+    constexpr int stepV = ord_rank(ORD, V) < K ? S : 2 * S;
+    constexpr int nU = count_on(ext_of(U), stepU);
+    constexpr int v0 = (V == 0 && CARRIED) ? 1 : 0;  // plane 0 carried: its lines are done
+    constexpr int nV = count_on(ext_of(V), stepV) - v0;
+    constexpr int NC = chunks_of(D);
+    constexpr int NSEG = nU * nV * NC;
+    constexpr int BD = bstride(D), BU = bstride(U), BV = bstride(V);
+    constexpr int KD = cstride(D), KU = cstride(U), KV = cstride(V);
+    // after the last pass of compression only plane 8 (carried to the next slab) is read again
+    constexpr bool LAST = COMPRESS && S == 1 && K == 2;
+#pragma unroll 1
+    for (int w = (int)threadIdx.x; w < NSEG; w += NT) {
+        const int q1 = w / nU;
+        const int iu = w - q1 * nU;
+        const int cd = NC == 1 ? 0 : q1 / nV;
+        const int iv = q1 - cd * nV + v0;
+        const int u = iu * stepU, v = iv * stepV;
+        float *L = c.box + v * BV + u * BU + 8 * cd * BD;
+        uint16_t *C = c.codes + v * KV + u * KU + 8 * cd * KD;
+        const bool keep = !LAST || (D != 0 && v == 8);
+        if (cd < c.nfull[D]) seg_full<COMPRESS, S, BD, KD, SPLINE>(L, C, Lq, cub, cbias, Rf, keep);
+        else seg_trunc<COMPRESS, S, BD, KD>(L, C, c.rem[D] - 8 * cd, SPLINE, Lq, cub, cbias, Rf, keep);
+    }
+}
+
+template <bool COMPRESS, int ORD, bool CARRIED, int S>
+__device__ __forceinline__ void fast_level(const FastCtx &c, const Levels &lv)
+{
+    constexpr int l = S == 1 ? 0 : (S == 2 ? 1 : 2);
+    const LevelQ Lq = lv.L[l];
+    const bool spline = lv.spline[l] != 0;
+    const uint32_t cbias = lv.cbias;
+    const float Rf = lv.Rf;
+#define GI_FAST_PASS(K)                                                                                    \
+    {                                                                                                      \
+        const Cubic cub = lv.cub[ord_axis(ORD, K)];                                                        \
+        if (spline) fast_pass<COMPRESS, ORD, CARRIED, S, K, true>(c, Lq, cub, cbias, Rf);                  \
+        else fast_pass<COMPRESS, ORD, CARRIED, S, K, false>(c, Lq, cub, cbias, Rf);                        \
+        __syncthreads();                                                                                   \
+    }
+    GI_FAST_PASS(0)
+    GI_FAST_PASS(1)
+    GI_FAST_PASS(2)
+#undef GI_FAST_PASS
+}
+
+template <bool COMPRESS, int ORD>
+__device__ __forceinline__ void fast_slab(const FastCtx &c, const Levels &lv, bool carried)
+{
+    if (carried) {
+        fast_level<COMPRESS, ORD, true, 4>(c, lv);
+        fast_level<COMPRESS, ORD, true, 2>(c, lv);
+        fast_level<COMPRESS, ORD, true, 1>(c, lv);
+    } else {
+        fast_level<COMPRESS, ORD, false, 4>(c, lv);
+        fast_level<COMPRESS, ORD, false, 2>(c, lv);
+        fast_level<COMPRESS, ORD, false, 1>(c, lv);
+    }
+}
+
+// The nine passes of a slab in the default neighbour domain, every order.
+template <bool COMPRESS>
+__device__ __forceinline__ void fast_levels(float *box, uint16_t *codes, const Slab &sl, const Field &f,
+                                            const Levels &lv)
+{
+    FastCtx c;
+    c.box = box;
+    c.codes = codes;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c.rem[a] = f.n[a] - 1 - sl.g0[a];
+        c.nfull[a] = min(chunks_of(a), c.rem[a] / 8);
+    }
+    switch (lv.ord_id) {
+    case 0: fast_slab<COMPRESS, 0>(c, lv, sl.carried); break;
+    case 1: fast_slab<COMPRESS, 1>(c, lv, sl.carried); break;
+    case 2: fast_slab<COMPRESS, 2>(c, lv, sl.carried); break;
+    case 3: fast_slab<COMPRESS, 3>(c, lv, sl.carried); break;
+    case 4: fast_slab<COMPRESS, 4>(c, lv, sl.carried); break;
+    default: fast_slab<COMPRESS, 5>(c, lv, sl.carried); break;
+    }
+}
+
 // The x-extended domain is an option: compression instantiates a kernel with it
 // only when a field asks for it (XDOM); decompression, whose configuration is on
 // the device, reaches it through an out-of-line call so that the default passes
@@ -379,12 +582,13 @@ template <bool COMPRESS, bool XDOM>
 __device__ __forceinline__ void run_slab(float *box, const Sink &sk, const Slab &sl, const Field &f,
                                          const Levels &lv)
 {
+    uint16_t *codes = COMPRESS ? sk.stage : const_cast<uint16_t *>(sk.cbox);
     if (COMPRESS) {
         if (XDOM && lv.xdom32) run_levels<COMPRESS, XDOM>(box, sk, sl, f, lv);
-        else run_levels<COMPRESS, false>(box, sk, sl, f, lv);
+        else fast_levels<COMPRESS>(box, codes, sl, f, lv);
     } else {
         if (lv.xdom32) run_levels_xdom<COMPRESS>(box, sk, sl, f, lv);
-        else run_levels<COMPRESS, false>(box, sk, sl, f, lv);
+        else fast_levels<COMPRESS>(box, codes, sl, f, lv);
     }
 }
 
@@ -793,7 +997,7 @@ struct DBatch {
 };
 
 template <bool MULTI>
-__global__ void __launch_bounds__(NT) k_decompress(const __grid_constant__ DBatch B)
+__global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_constant__ DBatch B)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ Levels lv;

@@ -247,7 +247,8 @@ int interp_compress_batched(const interp_compress_item *items, int n, interp_str
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         const interp_compress_item &it = items[i];
         e = gi::launch_outlier_compaction(args[i].bitmap, args[i].blockcnt, L[i].words, args[i].dims, it.d_x,
-                                          it.d_out_idx, it.d_out_val, it.out_capacity, it.d_hdr, s);
+                                          it.d_out_idx, it.d_out_val, it.out_capacity, it.d_hdr, s, false,
+                                          it.d_hist, it.cfg.radius);  // the tile kernel leaves bin R to it
     }
     return cuda_status(e);
 }

@@ -175,7 +175,8 @@ cudaError_t launch_nd_compress(int ndim, const CompressArgs &a, cudaStream_t s);
 cudaError_t launch_nd_decompress(int ndim, const DecompressArgs &a, cudaStream_t s);
 cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
                                       const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
-                                      interp_header *hdr, cudaStream_t s, bool row_major = false);
+                                      interp_header *hdr, cudaStream_t s, bool row_major = false,
+                                      uint32_t *central_hist = nullptr, int radius = 0);  // fills bin R
 cudaError_t launch_outlier_scatter(const interp_header *hdr, const uint32_t *idx, const float *val,
                                    uint64_t capacity, float *xrec, cudaStream_t s);
 cudaError_t launch_histogram(const uint16_t *codes, uint64_t n, int radius, uint32_t *hist, cudaStream_t s);

@@ -18,9 +18,12 @@ constexpr int WRITE_THREADS = 256;
 constexpr int WORDS_PER_THREAD = BITMAP_BLOCK_WORDS / WRITE_THREADS;  // 8
 static_assert(WORDS_PER_THREAD * WRITE_THREADS == BITMAP_BLOCK_WORDS, "block geometry");
 
-// Exclusive scan of the block counts in place; total -> header.
+// Exclusive scan of the block counts in place; total -> header.  With a
+// histogram whose central bin R the tile kernel left out (it is the most
+// frequent code by far), the bin is filled in here: N minus every other bin.
 __global__ void __launch_bounds__(SCAN_THREADS) k_outlier_scan(uint32_t *blockcnt, int nblk, interp_header *hdr,
-                                                              unsigned long long capacity)
+                                                              unsigned long long capacity, uint32_t *hist,
+                                                              int radius, unsigned long long n)
 {
     __shared__ unsigned long long warp_sum[SCAN_THREADS / 32];
     __shared__ unsigned long long carry;
@@ -58,6 +61,21 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_outlier_scan(uint32_t *blockcn
     if (threadIdx.x == 0) {
         hdr->n_outliers = carry;
         if (carry > capacity) hdr->status |= INTERP_STATUS_CAPACITY;
+    }
+    if (hist) {
+        unsigned long long others = 0;
+        for (int c = threadIdx.x; c < 2 * radius; c += SCAN_THREADS)
+            if (c != radius) others += hist[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) others += __shfl_xor_sync(0xffffffffu, others, off);
+        __syncthreads();
+        if (lane == 0) warp_sum[warp] = others;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < SCAN_THREADS / 32; ++w) t += warp_sum[w];
+            hist[radius] = (uint32_t)(n - t);
+        }
     }
 }
 
@@ -191,11 +209,14 @@ __global__ void __launch_bounds__(HIST_THREADS) k_histogram(const uint16_t *__re
 
 cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
                                       const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
-                                      interp_header *hdr, cudaStream_t s, bool row_major)
+                                      interp_header *hdr, cudaStream_t s, bool row_major, uint32_t *central_hist,
+                                      int radius)
 {
     const int nblk = (int)((words + BITMAP_BLOCK_WORDS - 1) / BITMAP_BLOCK_WORDS);
     if (nblk <= 0) return cudaSuccess;
-    k_outlier_scan<<<1, SCAN_THREADS, 0, s>>>(blockcnt, nblk, hdr, (unsigned long long)capacity);
+    const unsigned long long n = (unsigned long long)d.nz * d.ny * d.nx;
+    k_outlier_scan<<<1, SCAN_THREADS, 0, s>>>(blockcnt, nblk, hdr, (unsigned long long)capacity, central_hist,
+                                              radius, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int words_per_row = (d.nx + 31) / 32;

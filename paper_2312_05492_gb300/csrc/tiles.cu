@@ -55,6 +55,9 @@ __host__ __device__ constexpr int own_of(int a) { return a == 2 ? OX : (a == 1 ?
 __host__ __device__ constexpr int bstride(int a) { return a == 2 ? 1 : (a == 1 ? EX : PLANE); }
 __host__ __device__ constexpr int sstride(int a) { return a == 2 ? 1 : (a == 1 ? CP : STAGE_PLANE); }
 __host__ __device__ constexpr int cstride(int a) { return a == 2 ? 1 : (a == 1 ? CP : CBOX_PLANE); }
+// decompression reads the codes where the TMA landed them: rows of KP codes, planes of EY rows
+__host__ __device__ constexpr int lstride(int a) { return a == 2 ? 1 : (a == 1 ? KP : EY * KP); }
+static_assert((KP * 2) % 16 == 0, "landed code rows stay 16-byte aligned");
 __host__ __device__ constexpr int chunks_of(int a) { return a == 2 ? OX / 8 : (a == 1 ? OY / 8 : 1); }
 __host__ __device__ constexpr int axis_u(int d) { return d == 2 ? 1 : 2; }  // faster other axis
 __host__ __device__ constexpr int axis_v(int d) { return d == 0 ? 1 : 0; }
@@ -76,13 +79,19 @@ constexpr size_t C_LAND = 0;
 constexpr size_t C_STAGE = C_LAND;
 constexpr size_t C_BOX = al16(C_LAND + sizeof(float) * XLAND);
 constexpr size_t C_HIST = al16(C_BOX + sizeof(float) * BOXF);
-constexpr size_t C_BAR = al16(C_HIST + sizeof(uint32_t) * HIST_SMEM_BINS);
+// histogram bins, then one spare word per lane that takes the updates a point
+// does not count (a predicated update would become a branch per point)
+constexpr int HIST_WORDS = HIST_SMEM_BINS + 32;
+constexpr size_t C_BAR = al16(C_HIST + sizeof(uint32_t) * HIST_WORDS);
 constexpr size_t kCompressSmem = C_BAR + 16;
 static_assert(sizeof(uint16_t) * STAGE <= sizeof(float) * XLAND, "staged codes fit the landing buffer");
+// decompression: two code landing buffers (the next slab's codes land while the
+// current slab's passes read theirs), then the value box and one barrier per buffer
+__host__ __device__ constexpr size_t al128(size_t v) { return (v + 127) / 128 * 128; }
 constexpr size_t D_LAND = 0;
-constexpr size_t D_BOX = al16(D_LAND + sizeof(uint16_t) * KLAND);
-constexpr size_t D_CBOX = al16(D_BOX + sizeof(float) * BOXF);
-constexpr size_t D_BAR = al16(D_CBOX + sizeof(uint16_t) * CBOX);
+constexpr size_t D_LANDB = al128(sizeof(uint16_t) * KLAND);  // bytes per landing buffer
+constexpr size_t D_BOX = 2 * D_LANDB;
+constexpr size_t D_BAR = al16(D_BOX + sizeof(float) * BOXF);
 constexpr size_t kDecompressSmem = D_BAR + 16;
 // with 16-row columns, 5 compression CTAs fit an SM: dynamic + static (< 512 B) + 1 KB reserved each
 constexpr int kCompressCtas = 5;
@@ -115,6 +124,8 @@ struct Slab {
     int col;             // column index (cy * cols_x + cx)
     bool carried;        // plane 0 carried from the previous slab (not recomputed)
     int own_lo, own_hi;  // local planes whose outputs this slab writes
+    int lim[3];          // per axis: box positions below lim are owned and inside the field
+                         // (z: planes up to own_hi; y, x: owned rows / columns)
 };
 
 // Per-call constants, one copy in shared memory.
@@ -130,7 +141,18 @@ struct Levels {
     int xdom32;      // neighbour domain along x: the column's 32-point block (else the chunk)
     int nseg[2][3][3];  // segments of pass k of level l, [plane 0 carried][l][k]
     int ord_id;         // index of the axis order (ord_axis)
+    // the same values packed for single 16-byte loads in the fixed-geometry passes
+    float4 q4[3];       // per level: e, 2e, 1/(2e), spline (0 or 1)
+    float4 cub4[3];     // per axis: cubic coefficients a, b, c
+    uint4 k4;           // R, float(R) bits, cbias
 };
+
+// Dynamic shared memory of the tile kernels (layouts C_* and D_* above).
+extern __shared__ __align__(128) unsigned char g_smem[];
+
+// The kernels' copy of the per-call constants (one per CTA).  The pass functions
+// read it by name, so its accesses stay shared-memory loads in out-of-line code.
+__shared__ Levels g_lv;
 
 __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
 {
@@ -148,6 +170,11 @@ __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
     lv.Rf = (float)lv.R;
     lv.cbias = kMagicBits - (uint32_t)lv.R;
     lv.xdom32 = h->cfg.domain_x == 32;
+    for (int l = 0; l < 3; ++l) {
+        lv.q4[l] = make_float4(lv.L[l].e, lv.L[l].twoe, lv.L[l].inv2e, lv.spline[l] ? 1.0f : 0.0f);
+        lv.cub4[l] = make_float4(lv.cub[l].a, lv.cub[l].b, lv.cub[l].c, 0.0f);
+    }
+    lv.k4 = make_uint4((uint32_t)lv.R, __float_as_uint(lv.Rf), lv.cbias, 0u);
     // segment counts of every pass (the same rule as run_pass), so that threads
     // without work in a pass leave it at once
     for (int carried = 0; carried < 2; ++carried)
@@ -177,13 +204,31 @@ __device__ __forceinline__ void slab_setup(Slab &s, const Field &f, int item, in
     s.own_lo = s.carried ? 1 : 0;
     const bool field_end = 8 * c + 8 == f.n[0] - 1;
     s.own_hi = (c != c_last || field_end) ? 8 : 7;
+    s.lim[0] = min(s.own_hi, f.n[0] - 1 - s.g0[0]) + 1;
+    s.lim[1] = min(OY, f.n[1] - s.g0[1]);
+    s.lim[2] = min(OX, f.n[2] - s.g0[2]);
 }
 
 // ------------------------------------------------------------ passes
 struct Sink {
     uint16_t *stage;       // compression: code staging
-    const uint16_t *cbox;  // decompression: code box
+    const uint16_t *cbox;  // decompression: the slab's landed codes
+    uint32_t *hist_s;      // compression: shared bins of codes 0 .. HIST_SMEM_BINS - 1
+    uint32_t *hist_g;      // compression: global bins (codes beyond the shared ones), may be null
 };
+
+// Histogram of one owned point's code (Fig. 1, Sec. V-A).  The central code R
+// is not counted: it is by far the most frequent one, and its bin is filled in
+// after the tile kernel as N minus the other bins.  Code 0 (outliers) always
+// lands in shared memory, which also tells the write-out whether a slab has
+// outliers at all.
+__device__ __forceinline__ void count_code(const Sink &sk, uint32_t code, uint32_t R, bool owned)
+{
+    if (owned && code != R) {
+        if (code < (uint32_t)HIST_SMEM_BINS) atomicAdd(sk.hist_s + code, 1u);
+        else if (sk.hist_g) atomicAdd(sk.hist_g + code, 1u);
+    }
+}
 
 // INTERIOR: the slab's whole box lies inside the field and every chunk is
 // full, so no line or chunk needs the field-edge checks.
@@ -196,7 +241,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
     constexpr int NC = chunks_of(D);
     constexpr int BD = bstride(D), BU = bstride(U), BV = bstride(V);
     constexpr int SD = sstride(D), SU = sstride(U), SV = sstride(V);
-    constexpr int KD = cstride(D), KU = cstride(U), KV = cstride(V);
+    constexpr int KD = lstride(D), KU = lstride(U), KV = lstride(V);
     constexpr int l = S == 1 ? 0 : (S == 2 ? 1 : 2);
     if ((int)threadIdx.x >= lv.nseg[sl.carried ? 1 : 0][l][k]) return;  // no segment for this thread
 
@@ -233,6 +278,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
         if (!INTERIOR && (sl.g0[U] + u >= f.n[U] || sl.g0[V] + v >= f.n[V] || gd + S > f.n[D] - 1)) continue;
         float *line = box + v * BV + u * BU + dlo * BD;
         const bool owned = u < own_of(U) && v < own_of(V);
+        const bool counted = u < sl.lim[U] && v < sl.lim[V];  // owned and inside the field
         const int sbase = v * SV + u * SU + dlo * SD;
         const int cbase = v * KV + u * KU + dlo * KD;
 
@@ -243,6 +289,7 @@ __device__ __forceinline__ void run_pass(float *__restrict__ box, const Sink &sk
                 const uint32_t code = quantize(x, p, Lq, cbias, Rf, xr);
                 line[o * BD] = xr;
                 if (owned) sk.stage[sbase + o * SD] = (uint16_t)code;
+                count_code(sk, code, (uint32_t)lv.R, counted);
             } else {
                 // outliers (code 0) already hold their stored value in the box
                 const uint32_t code = sk.cbox[cbase + o * KD];
@@ -395,22 +442,33 @@ static_assert(ord_axis(0, 1) == 1 && ord_axis(0, 2) == 2 && ord_axis(1, 1) == 2 
 struct FastCtx {
     float *box;
     uint16_t *codes;  // code box: compression staging or decompression input (same layout)
+    uint32_t *hist;   // compression: shared histogram bins (every code is below HIST_SMEM_BINS)
     int nfull[3];     // chunks along each axis that end inside the field (full chunks)
     int rem[3];       // last in-field offset along each axis, from the box origin
+    int lim[3];       // owned in-field positions along each axis (Slab::lim)
 };
 
 // One point of a segment: compression quantizes and stages the code (the value
 // stays in the box unless no later pass or slab reads it); decompression applies
 // the stored code (code 0 = outlier, whose stored value is already in the box).
+struct SegOut {
+    uint32_t *hist;   // shared bins
+    uint32_t *spare;  // this lane's spare word (updates that count nothing)
+    uint32_t R;
+    bool keep;       // the value is read again (compression)
+    bool owned;      // the point's code is counted (compression)
+};
+
 template <bool COMPRESS>
 __device__ __forceinline__ void seg_emit(float *L, uint16_t *C, int ob, int oc, float p, const LevelQ &Lq,
-                                         uint32_t cbias, float Rf, bool keep)
+                                         uint32_t cbias, float Rf, const SegOut &so)
 {
     if (COMPRESS) {
         float xr;
         const uint32_t code = quantize(L[ob], p, Lq, cbias, Rf, xr);
-        if (keep) L[ob] = xr;
+        if (so.keep) L[ob] = xr;
         C[oc] = (uint16_t)code;
+        atomicAdd((so.owned && code != so.R) ? so.hist + code : so.spare, 1u);
     } else {
         const uint32_t code = C[oc];
         const float xq = p + code_to_q(code, cbias) * Lq.twoe;
@@ -418,31 +476,57 @@ __device__ __forceinline__ void seg_emit(float *L, uint16_t *C, int ob, int oc, 
     }
 }
 
+// Decompression with the code already in a register.
+__device__ __forceinline__ void seg_apply(float *L, int ob, float p, uint32_t code, const LevelQ &Lq, uint32_t cbias)
+{
+    const float xq = p + code_to_q(code, cbias) * Lq.twoe;
+    if (code) L[ob] = xq;
+}
+
 // A segment of a full chunk: the fixed stencils of Fig. 3 (SPLINE: cubic at
 // offsets 3 and 5, quadratics at 1 and 7 for stride 1; quadratics at stride 2;
 // stride 4 is always linear).
 template <bool COMPRESS, int S, int BD, int KD, bool SPLINE>
 __device__ __forceinline__ void seg_full(float *L, uint16_t *C, const LevelQ &Lq, const Cubic &cub, uint32_t cbias,
-                                         float Rf, bool keep)
+                                         float Rf, const SegOut &so)
 {
+    if (!COMPRESS && BD == 1 && KD == 1) {
+        // decompression along x: the chunk row's 8 codes are one aligned 16-byte word
+        // of the landed codes (rows of 80 bytes), so one load serves the segment
+        const uint4 w = *reinterpret_cast<const uint4 *>(C);
+        if (S == 4) {
+            seg_apply(L, 4, sp_linear(L[0], L[8]), w.z & 0xffffu, Lq, cbias);
+        } else if (S == 2) {
+            const float k0 = L[0], k4 = L[4], k8 = L[8];
+            seg_apply(L, 2, SPLINE ? sp_quad_right(k0, k4, k8) : sp_linear(k0, k4), w.y & 0xffffu, Lq, cbias);
+            seg_apply(L, 6, SPLINE ? sp_quad_left(k0, k4, k8) : sp_linear(k4, k8), w.w & 0xffffu, Lq, cbias);
+        } else {
+            const float k0 = L[0], k2 = L[2], k4 = L[4], k6 = L[6], k8 = L[8];
+            seg_apply(L, 1, SPLINE ? sp_quad_right(k0, k2, k4) : sp_linear(k0, k2), w.x >> 16, Lq, cbias);
+            seg_apply(L, 3, SPLINE ? sp_cubic(cub, k0, k2, k4, k6) : sp_linear(k2, k4), w.y >> 16, Lq, cbias);
+            seg_apply(L, 5, SPLINE ? sp_cubic(cub, k2, k4, k6, k8) : sp_linear(k4, k6), w.z >> 16, Lq, cbias);
+            seg_apply(L, 7, SPLINE ? sp_quad_left(k4, k6, k8) : sp_linear(k6, k8), w.w >> 16, Lq, cbias);
+        }
+        return;
+    }
     if (S == 4) {
-        seg_emit<COMPRESS>(L, C, 4 * BD, 4 * KD, sp_linear(L[0], L[8 * BD]), Lq, cbias, Rf, keep);
+        seg_emit<COMPRESS>(L, C, 4 * BD, 4 * KD, sp_linear(L[0], L[8 * BD]), Lq, cbias, Rf, so);
     } else if (S == 2) {
         const float k0 = L[0], k4 = L[4 * BD], k8 = L[8 * BD];
         seg_emit<COMPRESS>(L, C, 2 * BD, 2 * KD, SPLINE ? sp_quad_right(k0, k4, k8) : sp_linear(k0, k4), Lq, cbias,
-                           Rf, keep);
+                           Rf, so);
         seg_emit<COMPRESS>(L, C, 6 * BD, 6 * KD, SPLINE ? sp_quad_left(k0, k4, k8) : sp_linear(k4, k8), Lq, cbias,
-                           Rf, keep);
+                           Rf, so);
     } else {
         const float k0 = L[0], k2 = L[2 * BD], k4 = L[4 * BD], k6 = L[6 * BD], k8 = L[8 * BD];
         seg_emit<COMPRESS>(L, C, BD, KD, SPLINE ? sp_quad_right(k0, k2, k4) : sp_linear(k0, k2), Lq, cbias, Rf,
-                           keep);
+                           so);
         seg_emit<COMPRESS>(L, C, 3 * BD, 3 * KD, SPLINE ? sp_cubic(cub, k0, k2, k4, k6) : sp_linear(k2, k4), Lq,
-                           cbias, Rf, keep);
+                           cbias, Rf, so);
         seg_emit<COMPRESS>(L, C, 5 * BD, 5 * KD, SPLINE ? sp_cubic(cub, k2, k4, k6, k8) : sp_linear(k4, k6), Lq,
-                           cbias, Rf, keep);
+                           cbias, Rf, so);
         seg_emit<COMPRESS>(L, C, 7 * BD, 7 * KD, SPLINE ? sp_quad_left(k4, k6, k8) : sp_linear(k6, k8), Lq, cbias,
-                           Rf, keep);
+                           Rf, so);
     }
 }
 
@@ -450,7 +534,7 @@ __device__ __forceinline__ void seg_full(float *L, uint16_t *C, const LevelQ &Lq
 // the neighbour-count rule point by point (Sec. IV-B.1).
 template <bool COMPRESS, int S, int BD, int KD>
 __device__ __forceinline__ void seg_trunc(float *L, uint16_t *C, int hi, bool spline, const LevelQ &Lq,
-                                          const Cubic &cub, uint32_t cbias, float Rf, bool keep)
+                                          const Cubic &cub, uint32_t cbias, float Rf, const SegOut &so)
 {
 #pragma unroll
     for (int o = S; o < 8; o += 2 * S) {
@@ -470,16 +554,24 @@ __device__ __forceinline__ void seg_trunc(float *L, uint16_t *C, int hi, bool sp
             else if (has_p3) p = sp_quad_right(m1, p1, L[(o + 3 * S) * BD]);
             else p = sp_linear(m1, p1);
         }
-        seg_emit<COMPRESS>(L, C, o * BD, o * KD, p, Lq, cbias, Rf, keep);
+        seg_emit<COMPRESS>(L, C, o * BD, o * KD, p, Lq, cbias, Rf, so);
     }
 }
 
+// Constants of one fixed-geometry pass.
+struct PassK {
+    LevelQ Lq;
+    Cubic cub;
+    uint32_t cbias;
+    float Rf;
+    uint32_t R;
+};
+
 // Pass k of the level of stride S for axis order ORD.  Segments are numbered with
 // U (the faster other axis) fastest, then V, then the chunk along D; thread t
-// takes segments t, t + NT, ...
+// takes segments t, t + NT, ...  Threads without a segment skip the pass at once.
 template <bool COMPRESS, int ORD, bool CARRIED, int S, int K, bool SPLINE>
-__device__ __forceinline__ void fast_pass(const FastCtx &c, const LevelQ &Lq, const Cubic &cub, uint32_t cbias,
-                                          float Rf)
+__device__ __forceinline__ void fast_pass(const FastCtx &c, const PassK &pk)
 {
     constexpr int D = ord_axis(ORD, K);
     constexpr int U = axis_u(D), V = axis_v(D);
@@ -491,9 +583,20 @@ __device__ __forceinline__ void fast_pass(const FastCtx &c, const LevelQ &Lq, co
     constexpr int NC = chunks_of(D);
     constexpr int NSEG = nU * nV * NC;
     constexpr int BD = bstride(D), BU = bstride(U), BV = bstride(V);
-    constexpr int KD = cstride(D), KU = cstride(U), KV = cstride(V);
+    // codes: compression stages them in the code-box layout, decompression reads them as landed
+    constexpr int KD = COMPRESS ? cstride(D) : lstride(D), KU = COMPRESS ? cstride(U) : lstride(U),
+                  KV = COMPRESS ? cstride(V) : lstride(V);
     // after the last pass of compression only plane 8 (carried to the next slab) is read again
     constexpr bool LAST = COMPRESS && S == 1 && K == 2;
+    Cubic cub = pk.cub;
+    if (S == 1 && SPLINE) {  // the pass axis's cubic
+        const float4 k = g_lv.cub4[D];
+        cub = Cubic{k.x, k.y, k.z};
+    }
+    SegOut so;
+    so.hist = c.hist;
+    so.spare = c.hist + HIST_SMEM_BINS + (threadIdx.x & 31);
+    so.R = pk.R;
 #pragma unroll 1
     for (int w = (int)threadIdx.x; w < NSEG; w += NT) {
         const int q1 = w / nU;
@@ -503,93 +606,124 @@ __device__ __forceinline__ void fast_pass(const FastCtx &c, const LevelQ &Lq, co
         const int u = iu * stepU, v = iv * stepV;
         float *L = c.box + v * BV + u * BU + 8 * cd * BD;
         uint16_t *C = c.codes + v * KV + u * KU + 8 * cd * KD;
-        const bool keep = !LAST || (D != 0 && v == 8);
-        if (cd < c.nfull[D]) seg_full<COMPRESS, S, BD, KD, SPLINE>(L, C, Lq, cub, cbias, Rf, keep);
-        else seg_trunc<COMPRESS, S, BD, KD>(L, C, c.rem[D] - 8 * cd, SPLINE, Lq, cub, cbias, Rf, keep);
+        so.keep = !LAST || (D != 0 && v == 8);
+        so.owned = u < c.lim[U] && v < c.lim[V];
+        if (cd < c.nfull[D]) seg_full<COMPRESS, S, BD, KD, SPLINE>(L, C, pk.Lq, cub, pk.cbias, pk.Rf, so);
+        else seg_trunc<COMPRESS, S, BD, KD>(L, C, c.rem[D] - 8 * cd, SPLINE, pk.Lq, cub, pk.cbias, pk.Rf, so);
     }
+}
+
+template <bool COMPRESS, int ORD, bool CARRIED, int S, int K>
+__device__ __forceinline__ void fast_pass_any(const FastCtx &c, const PassK &pk, bool spline)
+{
+    constexpr int D = ord_axis(ORD, K);
+    constexpr int U = axis_u(D), V = axis_v(D);
+    constexpr int nU = count_on(ext_of(U), ord_rank(ORD, U) < K ? S : 2 * S);
+    constexpr int nV = count_on(ext_of(V), ord_rank(ORD, V) < K ? S : 2 * S) - ((V == 0 && CARRIED) ? 1 : 0);
+    if ((int)threadIdx.x < nU * nV * chunks_of(D)) {
+        if (spline) fast_pass<COMPRESS, ORD, CARRIED, S, K, true>(c, pk);
+        else fast_pass<COMPRESS, ORD, CARRIED, S, K, false>(c, pk);
+    }
+    __syncthreads();
 }
 
 template <bool COMPRESS, int ORD, bool CARRIED, int S>
-__device__ __forceinline__ void fast_level(const FastCtx &c, const Levels &lv)
+__device__ __forceinline__ void fast_level(const FastCtx &c, PassK pk)
 {
     constexpr int l = S == 1 ? 0 : (S == 2 ? 1 : 2);
-    const LevelQ Lq = lv.L[l];
-    const bool spline = lv.spline[l] != 0;
-    const uint32_t cbias = lv.cbias;
-    const float Rf = lv.Rf;
-#define GI_FAST_PASS(K)                                                                                    \
-    {                                                                                                      \
-        const Cubic cub = lv.cub[ord_axis(ORD, K)];                                                        \
-        if (spline) fast_pass<COMPRESS, ORD, CARRIED, S, K, true>(c, Lq, cub, cbias, Rf);                  \
-        else fast_pass<COMPRESS, ORD, CARRIED, S, K, false>(c, Lq, cub, cbias, Rf);                        \
-        __syncthreads();                                                                                   \
-    }
-    GI_FAST_PASS(0)
-    GI_FAST_PASS(1)
-    GI_FAST_PASS(2)
-#undef GI_FAST_PASS
+    const float4 q = g_lv.q4[l];
+    pk.Lq = LevelQ{q.x, q.y, q.z};
+    const bool spline = q.w != 0.0f;
+    fast_pass_any<COMPRESS, ORD, CARRIED, S, 0>(c, pk, spline);
+    fast_pass_any<COMPRESS, ORD, CARRIED, S, 1>(c, pk, spline);
+    fast_pass_any<COMPRESS, ORD, CARRIED, S, 2>(c, pk, spline);
 }
 
 template <bool COMPRESS, int ORD>
-__device__ __forceinline__ void fast_slab(const FastCtx &c, const Levels &lv, bool carried)
+__device__ __forceinline__ void fast_slab(const FastCtx &c, const PassK &pk, bool carried)
 {
     if (carried) {
-        fast_level<COMPRESS, ORD, true, 4>(c, lv);
-        fast_level<COMPRESS, ORD, true, 2>(c, lv);
-        fast_level<COMPRESS, ORD, true, 1>(c, lv);
+        fast_level<COMPRESS, ORD, true, 4>(c, pk);
+        fast_level<COMPRESS, ORD, true, 2>(c, pk);
+        fast_level<COMPRESS, ORD, true, 1>(c, pk);
     } else {
-        fast_level<COMPRESS, ORD, false, 4>(c, lv);
-        fast_level<COMPRESS, ORD, false, 2>(c, lv);
-        fast_level<COMPRESS, ORD, false, 1>(c, lv);
+        fast_level<COMPRESS, ORD, false, 4>(c, pk);
+        fast_level<COMPRESS, ORD, false, 2>(c, pk);
+        fast_level<COMPRESS, ORD, false, 1>(c, pk);
     }
 }
 
 // The nine passes of a slab in the default neighbour domain, every order.
+// The nine passes of a slab in the default neighbour domain, every order.
+// rem: last in-field offset per axis from the box origin; lim: Slab::lim.
 template <bool COMPRESS>
-__device__ __forceinline__ void fast_levels(float *box, uint16_t *codes, const Slab &sl, const Field &f,
-                                            const Levels &lv)
+__device__ __forceinline__ void fast_levels(float *box, uint16_t *codes, uint32_t *hist, int rem0, int rem1,
+                                            int rem2, int lim0, int lim1, int lim2, bool carried, const Levels &lv)
 {
     FastCtx c;
     c.box = box;
     c.codes = codes;
+    c.hist = hist;
+    c.rem[0] = rem0;
+    c.rem[1] = rem1;
+    c.rem[2] = rem2;
+    c.lim[0] = lim0;
+    c.lim[1] = lim1;
+    c.lim[2] = lim2;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        c.rem[a] = f.n[a] - 1 - sl.g0[a];
-        c.nfull[a] = min(chunks_of(a), c.rem[a] / 8);
-    }
+    for (int a = 0; a < 3; ++a) c.nfull[a] = min(chunks_of(a), c.rem[a] / 8);
+    const uint4 k = lv.k4;
+    PassK pk;
+    pk.R = k.x;
+    pk.Rf = __uint_as_float(k.y);
+    pk.cbias = k.z;
+    pk.cub = Cubic{0.0f, 0.0f, 0.0f};
     switch (lv.ord_id) {
-    case 0: fast_slab<COMPRESS, 0>(c, lv, sl.carried); break;
-    case 1: fast_slab<COMPRESS, 1>(c, lv, sl.carried); break;
-    case 2: fast_slab<COMPRESS, 2>(c, lv, sl.carried); break;
-    case 3: fast_slab<COMPRESS, 3>(c, lv, sl.carried); break;
-    case 4: fast_slab<COMPRESS, 4>(c, lv, sl.carried); break;
-    default: fast_slab<COMPRESS, 5>(c, lv, sl.carried); break;
+    case 0: fast_slab<COMPRESS, 0>(c, pk, carried); break;
+    case 1: fast_slab<COMPRESS, 1>(c, pk, carried); break;
+    case 2: fast_slab<COMPRESS, 2>(c, pk, carried); break;
+    case 3: fast_slab<COMPRESS, 3>(c, pk, carried); break;
+    case 4: fast_slab<COMPRESS, 4>(c, pk, carried); break;
+    default: fast_slab<COMPRESS, 5>(c, pk, carried); break;
     }
 }
 
-// The x-extended domain is an option: compression instantiates a kernel with it
-// only when a field asks for it (XDOM); decompression, whose configuration is on
-// the device, reaches it through an out-of-line call so that the default passes
-// keep their code size.
+// Pass dispatch.  The fixed-geometry passes serve the default neighbour domain;
+// the x-extended domain (an option) and radii whose bins do not fit the shared
+// histogram take the general passes.  Both are out-of-line functions, compiled
+// once for every kernel that calls them (the call happens once per slab).
 template <bool COMPRESS>
-__device__ __noinline__ void run_levels_xdom(float *box, const Sink &sk, const Slab &sl, const Field &f,
-                                             const Levels &lv)
+__device__ __noinline__ void passes_fast(int code_off, int rem0, int rem1, int rem2, int lim0, int lim1, int lim2,
+                                         bool carried)
 {
-    run_levels<COMPRESS, true>(box, sk, sl, f, lv);
+    // pointers derived from the shared-memory symbol, so that every access is a shared one
+    float *box = reinterpret_cast<float *>(g_smem + (COMPRESS ? C_BOX : D_BOX));
+    uint16_t *codes = reinterpret_cast<uint16_t *>(g_smem + code_off);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(g_smem + C_HIST);
+    fast_levels<COMPRESS>(box, codes, hist, rem0, rem1, rem2, lim0, lim1, lim2, carried, g_lv);
 }
 
-template <bool COMPRESS, bool XDOM>
+template <bool COMPRESS>
+__device__ __noinline__ void passes_general(float *box, const Sink &sk, const Slab &sl, const Field &f)
+{
+    if (g_lv.xdom32) run_levels<COMPRESS, true>(box, sk, sl, f, g_lv);
+    else run_levels<COMPRESS, false>(box, sk, sl, f, g_lv);
+}
+
+template <bool COMPRESS>
 __device__ __forceinline__ void run_slab(float *box, const Sink &sk, const Slab &sl, const Field &f,
                                          const Levels &lv)
 {
-    uint16_t *codes = COMPRESS ? sk.stage : const_cast<uint16_t *>(sk.cbox);
-    if (COMPRESS) {
-        if (XDOM && lv.xdom32) run_levels<COMPRESS, XDOM>(box, sk, sl, f, lv);
-        else fast_levels<COMPRESS>(box, codes, sl, f, lv);
-    } else {
-        if (lv.xdom32) run_levels_xdom<COMPRESS>(box, sk, sl, f, lv);
-        else fast_levels<COMPRESS>(box, codes, sl, f, lv);
-    }
+    // compression: the fixed-geometry passes keep every code's bin in shared memory
+    const bool general = lv.xdom32 || (COMPRESS && 2 * lv.R > HIST_SMEM_BINS);
+    if (general)
+        passes_general<COMPRESS>(box, sk, sl, f);
+    else
+        passes_fast<COMPRESS>((int)((COMPRESS ? reinterpret_cast<const unsigned char *>(sk.stage)
+                                              : reinterpret_cast<const unsigned char *>(sk.cbox)) -
+                                    g_smem),
+                              f.n[0] - 1 - sl.g0[0], f.n[1] - 1 - sl.g0[1], f.n[2] - 1 - sl.g0[2], sl.lim[0],
+                              sl.lim[1], sl.lim[2], sl.carried);
 }
 
 // ------------------------------------------------------------ work list
@@ -705,8 +839,8 @@ struct CBatch {
 
 // Per-field values of the compression write-out, re-read when the field changes.
 struct CWrite {
-    int R, bins, Ay, Ax, WX;
-    bool smem_hist, vec_codes;
+    int R, Ay, Ax, WX;
+    bool vec_codes;
     int code_store;
 };
 
@@ -714,8 +848,6 @@ __device__ __forceinline__ CWrite cwrite_of(const CField &F)
 {
     CWrite w;
     w.R = F.a.radius;
-    w.bins = 2 * w.R;
-    w.smem_hist = F.a.hist != nullptr && w.bins <= HIST_SMEM_BINS;
     w.Ay = (F.f.n[1] - 1) / 8 + 1;
     w.Ax = (F.f.n[2] - 1) / 8 + 1;
     w.WX = (F.f.n[2] + 31) / 32;
@@ -725,43 +857,119 @@ __device__ __forceinline__ CWrite cwrite_of(const CField &F)
 }
 
 // Add the CTA's histogram counts of one field to its global bins and clear them.
-__device__ __forceinline__ void flush_hist(const CField &F, const CWrite &w, uint32_t *hist_s, uint32_t &central,
-                                           uint32_t *lane_ctrs)
+__device__ __forceinline__ void flush_hist(const CField &F, uint32_t *hist_s)
 {
-    const int lane = threadIdx.x & 31;
     __syncthreads();
-    if (threadIdx.x < 32) {  // fold the per-lane central counters into the register count
-        central += lane_ctrs[lane];
-        lane_ctrs[lane] = 0u;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) central += __shfl_xor_sync(0xffffffffu, central, off);
-    __syncthreads();
-    if (F.a.hist && lane == 0 && central) {
-        if (w.smem_hist) atomicAdd(&hist_s[w.R], central);
-        else atomicAdd(&F.a.hist[w.R], central);
-    }
-    central = 0;
-    __syncthreads();
-    if (w.smem_hist) {
-        for (int i = threadIdx.x; i < w.bins; i += NT) {
+    const int bins = min(2 * F.a.radius, HIST_SMEM_BINS);
+    if (F.a.hist)
+        for (int i = threadIdx.x; i < bins; i += NT) {
             const uint32_t h = hist_s[i];
             if (h) atomicAdd(&F.a.hist[i], h);
         }
-    }
     for (int i = threadIdx.x; i < HIST_SMEM_BINS; i += NT) hist_s[i] = 0u;
     __syncthreads();
 }
 
+// The owned planes of a slab whose rows all lie inside the field, with 16-byte
+// aligned code rows and no outlier: staged codes -> global (8 codes per thread
+// and store, three planes per step), anchors, and all-zero outlier-bitmap words.
+static_assert(NT % 4 == 0 && (NT / 4) % OY == 0, "write-out steps cover whole planes");
+__device__ __forceinline__ void write_slab_fast(const CField &F, const CWrite &cw, const Slab &sl, int rows,
+                                                const uint16_t *stage, const float *box)
+{
+    const Field &f = F.f;
+    constexpr int PSTEP = NT / 4 / OY;  // planes per step
+    const int sub = threadIdx.x & 3;
+    int r = threadIdx.x >> 2;
+    const int y = r % OY;
+    int pz = sl.own_lo + r / OY;
+    const size_t plane = (size_t)f.n[1] * f.n[2];
+    const uint16_t *sp = stage + pz * STAGE_PLANE + y * CP + 8 * sub;
+    uint16_t *gp = F.a.codes + ((size_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * f.n[2] + sl.g0[2] + 8 * sub;
+    const bool anchor_row = (y & 7) == 0;
+    for (; r < rows; r += NT / 4, pz += PSTEP, sp += PSTEP * STAGE_PLANE, gp += PSTEP * plane) {
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(sp);
+        uint32_t w0 = s32[0];
+        const uint32_t w1 = s32[1], w2 = s32[2], w3 = s32[3];
+        if (anchor_row && (pz & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
+            w0 = (w0 & 0xffff0000u) | (uint32_t)cw.R;
+            const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gx = sl.g0[2] + 8 * sub;
+            F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] = box[pz * PLANE + y * EX + 8 * sub];
+        }
+        *reinterpret_cast<uint4 *>(gp) = make_uint4(w0, w1, w2, w3);
+    }
+    // the slab's bitmap words are contiguous (16 per plane, tile-major layout)
+    uint32_t *wb = F.a.bitmap + ((size_t)sl.col * f.n[0] + sl.g0[0] + sl.own_lo) * OY;
+    if ((int)threadIdx.x < rows / 4) reinterpret_cast<uint4 *>(wb)[threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Any other slab: codes stored as alignment allows, anchors, and the exact
+// outlier-bitmap words with their block counts.  A warp takes 8 consecutive
+// rows of one plane, 4 lanes x 8 codes per row.
+__device__ __forceinline__ void write_slab_general(const CField &F, const CWrite &cw, const Slab &sl, int rows,
+                                                   const uint16_t *stage, const float *box)
+{
+    const Field &f = F.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane & 3;
+    for (int base = warp * 8; base < rows; base += NWARP * 8) {
+        const int row = base + (lane >> 2);
+        const int pz = sl.own_lo + row / OY, y = row % OY;
+        const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y;
+        const int gx = sl.g0[2] + 8 * sub;
+        const bool rin = row < rows && gy < f.n[1];
+        const int nvalid = rin ? min(8, f.n[2] - gx) : 0;  // in-field codes of this lane
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (row < rows) {
+            const uint32_t *srow = reinterpret_cast<const uint32_t *>(stage + pz * STAGE_PLANE + y * CP + 8 * sub);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = srow[j];
+        }
+        const size_t gi = ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
+        if (nvalid > 0 && ((pz | y) & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
+            w[0] = (w[0] & 0xffff0000u) | (uint32_t)cw.R;
+            F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] = box[pz * PLANE + y * EX + 8 * sub];
+        }
+        if (nvalid == 8 && cw.code_store == 8) {
+            *reinterpret_cast<uint4 *>(F.a.codes + gi) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else if (nvalid == 8 && cw.code_store == 4) {
+            reinterpret_cast<uint2 *>(F.a.codes + gi)[0] = make_uint2(w[0], w[1]);
+            reinterpret_cast<uint2 *>(F.a.codes + gi)[1] = make_uint2(w[2], w[3]);
+        } else if (nvalid == 8 && cw.code_store == 2) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) reinterpret_cast<uint32_t *>(F.a.codes + gi)[j] = w[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < nvalid) F.a.codes[gi + j] = (uint16_t)(w[j >> 1] >> (16 * (j & 1)));
+        }
+        // outlier bits (code 0) of this lane's in-field codes
+        uint32_t zmask = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            zmask |= (uint32_t)(j < nvalid && ((w[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) << j;
+        // the 4 lanes of a row assemble its 32-bit outlier word
+        uint32_t word = zmask << (8 * sub);
+        word |= __shfl_xor_sync(0xffffffffu, word, 1);
+        word |= __shfl_xor_sync(0xffffffffu, word, 2);
+        if (sub == 0 && rin) {
+            // tile-major bitmap: a slab's words are contiguous per plane
+            F.a.bitmap[((size_t)sl.col * f.n[0] + gz) * OY + y] = word;
+            if (word) {
+                const int64_t gw = ((int64_t)gz * f.n[1] + gy) * cw.WX + sl.g0[2] / 32;  // ascending order
+                atomicAdd(&F.a.blockcnt[gw / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
+            }
+        }
+    }
+}
+
 // MULTI = false: a single field (index 0 everywhere, resolved at compile time).
-// XDOM: some field of the launch uses the x-extended neighbour domain.
-template <bool MULTI, bool XDOM>
+template <bool MULTI>
 __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_constant__ CBatch B)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ Levels lv;
+    unsigned char *smem = g_smem;
+    Levels &lv = g_lv;
     __shared__ int abort_flag;
-    __shared__ uint32_t lane_ctrs[32];  // per-lane counters of the central code R (shared by the warps)
     float *land = reinterpret_cast<float *>(smem + C_LAND);
     float *box = reinterpret_cast<float *>(smem + C_BOX);
     uint16_t *stage = reinterpret_cast<uint16_t *>(smem + C_STAGE);
@@ -774,15 +982,10 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_con
         mbar_init(bar, 1);
         fence_barrier_init();
     }
-    for (int i = threadIdx.x; i < HIST_SMEM_BINS; i += NT) hist_s[i] = 0u;
-    if (threadIdx.x < 32) lane_ctrs[threadIdx.x] = 0u;
+    for (int i = threadIdx.x; i < HIST_WORDS; i += NT) hist_s[i] = 0u;
     __syncthreads();
 
-    uint32_t central = 0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t phase = 0;
-    const Sink sk{stage, nullptr};
-    uint32_t *const lane_ctr = lane_ctrs + lane;
 
     Cursor cu;
     if (!cursor_start<MULTI>(cu, bv, blockIdx.x)) return;
@@ -797,6 +1000,7 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_con
         const int fi = MULTI ? cu.fi : 0;
         const CField &F = B.fld[fi];
         const Field &f = F.f;
+        const Sink sk{stage, nullptr, hist_s, F.a.hist};
         Cursor nx = cu;
         const bool has_next = cursor_next<MULTI>(nx, bv);
         Slab sn = sl;
@@ -828,136 +1032,20 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_con
         }
         __syncthreads();  // box and levels ready; the landing buffer now stages codes
         if (abort_flag) break;
+        const uint32_t out0 = hist_s[0];  // outliers counted before this slab
 
-        run_slab<true, XDOM>(box, sk, sl, f, lv);  // ends with a barrier
+        run_slab<true>(box, sk, sl, f, lv);  // ends with a barrier
 
-        // ---- owned planes: codes (16-byte stores), anchors, histogram, bitmap words.
-        // A warp takes 8 consecutive rows of one plane, 4 lanes x 8 codes per row.
+        // ---- owned planes: codes, anchors, outlier-bitmap words
         const CWrite cw = cwrite_of(F);
         const int nzp = min(EZ, f.n[0] - sl.g0[0]);
         const int hi = min(sl.own_hi, nzp - 1);
         const int rows = (hi - sl.own_lo + 1) * OY;
-        const int sub = lane & 3;
-        // Fast path: every owned row of the slab lies inside the field, code rows are
-        // 16-byte aligned and the histogram bins fit in shared memory.
-        const bool fast = cw.smem_hist && sl.g0[1] + OY <= f.n[1] && sl.g0[2] + OX <= f.n[2];
-        if (fast) {
-            const size_t plane = (size_t)f.n[1] * f.n[2];
-            uint16_t *cb = F.a.codes + ((size_t)(sl.g0[0] + sl.own_lo) * f.n[1] + sl.g0[1]) * f.n[2] + sl.g0[2] +
-                           8 * sub;
-            uint32_t *wb = F.a.bitmap + ((size_t)sl.col * f.n[0] + sl.g0[0] + sl.own_lo) * OY;
-            const uint16_t *sb = stage + sl.own_lo * STAGE_PLANE + 8 * sub;
-            const uint32_t Ru = (uint32_t)cw.R;
-            for (int row = threadIdx.x >> 2; row < rows; row += NT / 4) {
-                const int pzr = row / OY, y = row % OY;
-                const uint32_t *srow = reinterpret_cast<const uint32_t *>(sb + pzr * STAGE_PLANE + y * CP);
-                uint32_t w[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) w[j] = srow[j];
-                const int pz = sl.own_lo + pzr;
-                if (((pz | y) & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
-                    w[0] = (w[0] & 0xffff0000u) | Ru;
-                    const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gx = sl.g0[2] + 8 * sub;
-                    F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] =
-                        box[pz * PLANE + y * EX + 8 * sub];
-                }
-                uint16_t *dst = cb + pzr * plane + (size_t)y * f.n[2];
-                if (cw.code_store == 8) {
-                    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-                } else if (cw.code_store == 4) {
-                    reinterpret_cast<uint2 *>(dst)[0] = make_uint2(w[0], w[1]);
-                    reinterpret_cast<uint2 *>(dst)[1] = make_uint2(w[2], w[3]);
-                } else if (cw.code_store == 2) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) reinterpret_cast<uint32_t *>(dst)[j] = w[j];
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) dst[j] = (uint16_t)(w[j >> 1] >> (16 * (j & 1)));
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {  // every staged code here is < 2R
-                    const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-                    atomicAdd(c == Ru ? lane_ctr : hist_s + c, 1u);
-                }
-                uint32_t zmask = 0;
-                if (has_zero_half(w[0]) | has_zero_half(w[1]) | has_zero_half(w[2]) | has_zero_half(w[3])) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        zmask |= (uint32_t)(((w[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) << j;
-                }
-                uint32_t word = zmask << (8 * sub);
-                word |= __shfl_xor_sync(0xffffffffu, word, 1);
-                word |= __shfl_xor_sync(0xffffffffu, word, 2);
-                if (sub == 0) {
-                    wb[row] = word;
-                    if (word) {
-                        const int64_t gw = ((int64_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * cw.WX + sl.g0[2] / 32;
-                        atomicAdd(&F.a.blockcnt[gw / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
-                    }
-                }
-            }
-        }
-        for (int base = warp * 8; !fast && base < rows; base += NWARP * 8) {
-            const int row = base + (lane >> 2);
-            const int pz = sl.own_lo + row / OY, y = row % OY;
-            const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y;
-            const int gx = sl.g0[2] + 8 * sub;
-            const bool rin = gy < f.n[1];
-            const int nvalid = rin ? min(8, f.n[2] - gx) : 0;  // in-field codes of this lane
-            const uint32_t *srow = reinterpret_cast<const uint32_t *>(stage + pz * STAGE_PLANE + y * CP + 8 * sub);
-            uint32_t w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) w[j] = srow[j];
-            const size_t gi = ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
-            if (nvalid > 0 && ((pz | y) & 7) == 0) {  // anchor at x = 8*sub (Sec. IV-A): lossless, code R
-                w[0] = (w[0] & 0xffff0000u) | (uint32_t)cw.R;
-                F.a.anchors[((size_t)(gz / 8) * cw.Ay + gy / 8) * cw.Ax + gx / 8] =
-                    box[pz * PLANE + y * EX + 8 * sub];
-            }
-            // codes to global memory
-            if (nvalid == 8 && cw.vec_codes) {
-                *reinterpret_cast<uint4 *>(F.a.codes + gi) = make_uint4(w[0], w[1], w[2], w[3]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (j < nvalid) F.a.codes[gi + j] = (uint16_t)(w[j >> 1] >> (16 * (j & 1)));
-            }
-            // outlier bits and histogram, one predicated atomic per code: the central
-            // code R (the most frequent one) goes to this lane's private counter
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t c = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-                const bool valid = j < nvalid;
-                if (cw.smem_hist) {
-                    uint32_t *bin = c == (uint32_t)cw.R ? lane_ctr : hist_s + c;
-                    if (valid && c < (uint32_t)cw.bins) atomicAdd(bin, 1u);
-                } else if (valid && F.a.hist && c < (uint32_t)cw.bins) {
-                    if (c == (uint32_t)cw.R) ++central;
-                    else atomicAdd(&F.a.hist[c], 1u);
-                }
-            }
-            // outlier bits (code 0), exact per code only when a word holds a zero half
-            // or the lane's codes are cut by the field's edge
-            uint32_t zmask = 0;  // bit j: code j of this lane is an outlier
-            if ((has_zero_half(w[0]) | has_zero_half(w[1]) | has_zero_half(w[2]) | has_zero_half(w[3])) ||
-                nvalid < 8) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    zmask |= (uint32_t)(j < nvalid && ((w[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) << j;
-            }
-            // the 4 lanes of a row assemble its 32-bit outlier word
-            uint32_t word = zmask << (8 * sub);
-            word |= __shfl_xor_sync(0xffffffffu, word, 1);
-            word |= __shfl_xor_sync(0xffffffffu, word, 2);
-            if (sub == 0 && rin) {
-                // tile-major bitmap: a slab's words are contiguous per plane
-                F.a.bitmap[((size_t)sl.col * f.n[0] + gz) * OY + y] = word;
-                if (word) {
-                    const int64_t gw = ((int64_t)gz * f.n[1] + gy) * cw.WX + sl.g0[2] / 32;  // ascending order
-                    atomicAdd(&F.a.blockcnt[gw / BITMAP_BLOCK_WORDS], (uint32_t)__popc(word));
-                }
-            }
-        }
+        const bool outliers = hist_s[0] != out0;
+        if (!outliers && cw.code_store == 8 && sl.g0[1] + OY <= f.n[1] && sl.g0[2] + OX <= f.n[2])
+            write_slab_fast(F, cw, sl, rows, stage, box);
+        else
+            write_slab_general(F, cw, sl, rows, stage, box);
         // ---- next slab's input into the landing buffer (staged codes written out),
         // and plane 8 carried into plane 0 when the next slab continues this run
         __syncthreads();
@@ -969,15 +1057,20 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_compress(const __grid_con
                 for (int i = threadIdx.x; i < PLANE; i += NT) box[i] = box[8 * PLANE + i];
         }
         __syncthreads();  // box free for the next slab
-        if (!has_next || (MULTI && nx.fi != cu.fi)) flush_hist(F, cw, hist_s, central, lane_ctrs);  // field done
+        if (!has_next || (MULTI && nx.fi != cu.fi)) flush_hist(F, hist_s);  // field done
         if (!has_next) break;
         cu = nx;
         sl = sn;
     }
     if (abort_flag) {
         const int fi = MULTI ? cu.fi : 0;
-        if (threadIdx.x == 0) atomicOr(&B.fld[fi].a.hdr->status, INTERP_STATUS_TIMEOUT);
-        flush_hist(B.fld[fi], cwrite_of(B.fld[fi]), hist_s, central, lane_ctrs);
+        if (threadIdx.x == 0) {
+            atomicOr(&B.fld[fi].a.hdr->status, INTERP_STATUS_TIMEOUT);
+            // the transfer that did not arrive gets a second bounded wait before the
+            // CTA's shared memory is released
+            if (B.fld[fi].use_tma) mbar_wait_bounded(bar, phase ^ 1u, kTmaPolls);
+        }
+        flush_hist(B.fld[fi], hist_s);
     }
     cp_async_wait_all();
 }
@@ -996,51 +1089,91 @@ struct DBatch {
     int n, items;
 };
 
+// Decompression.  The codes of a slab land (TMA) in one of two buffers while the
+// previous slab is reconstructed from the other; the passes read them in place.
+// The anchors of the next slab are fetched into registers before the current
+// slab's passes, so that no global-memory latency sits between two slabs.
 template <bool MULTI>
 __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_constant__ DBatch B)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ Levels lv;
+    unsigned char *smem = g_smem;
+    Levels &lv = g_lv;
     __shared__ int abort_flag;
-    uint16_t *land = reinterpret_cast<uint16_t *>(smem + D_LAND);
     float *box = reinterpret_cast<float *>(smem + D_BOX);
-    uint16_t *cbox = reinterpret_cast<uint16_t *>(smem + D_CBOX);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + D_BAR);
     const BatchView<DField> bv{B.fld, B.n, B.items};
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_barrier_init();
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t phase = 0;
-    const Sink sk{nullptr, cbox};
+    uint32_t phase[2] = {0u, 0u};
+    auto land_of = [&](int b) { return reinterpret_cast<uint16_t *>(smem + D_LAND + b * D_LANDB); };
+
+    // anchors of a slab's planes 8 and (when not carried) 0: thread t < 2 * AYN * AXN holds one
+    constexpr int AYN = OY / 8 + 1, AXN = OX / 8 + 1;  // anchor rows / columns of the box
+    const int ai = threadIdx.x;
+    const int a_z = ai / (AYN * AXN), a_y = (ai / AXN) % AYN, a_x = ai % AXN;
+    const int a_off = (8 * a_z) * PLANE + (8 * a_y) * EX + 8 * a_x;
+    auto anchor_fetch = [&](const DField &F, const Slab &s, float &v) {
+        const Field &f = F.f;
+        const int pz = 8 * a_z, y = 8 * a_y, x = 8 * a_x;
+        const bool ok = ai < 2 * AYN * AXN && !(a_z == 0 && s.carried) && s.g0[0] + pz < f.n[0] &&
+                        s.g0[1] + y < f.n[1] && s.g0[2] + x < f.n[2];
+        if (ok) {
+            const int Ay = (f.n[1] - 1) / 8 + 1, Ax = (f.n[2] - 1) / 8 + 1;
+            v = __ldg(F.a.anchors + ((size_t)((s.g0[0] + pz) / 8) * Ay + (s.g0[1] + y) / 8) * Ax + (s.g0[2] + x) / 8);
+        }
+        return ok;
+    };
 
     Cursor cu;
     if (!cursor_start<MULTI>(cu, bv, blockIdx.x)) return;
     Slab sl;
     slab_of<MULTI>(sl, cu, bv);
     int lv_field = -1;
+    int buf = 0;
+    bool pending_next = false;  // the next slab's transfer was issued and not yet waited for
+    float anc = 0.0f;
+    bool anc_ok;
     {
         const int fi = MULTI ? cu.fi : 0;
-        issue_land<uint16_t, KP, EZ, 0>(land, B.fld[fi].a.codes, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f, sl);
+        issue_land<uint16_t, KP, EZ, 0>(land_of(0), B.fld[fi].a.codes, &B.map[fi], B.fld[fi].use_tma, &bar[0],
+                                        B.fld[fi].f, sl);
+        anc_ok = anchor_fetch(B.fld[fi], sl, anc);
     }
     for (;;) {
         const int fi = MULTI ? cu.fi : 0;
         const DField &F = B.fld[fi];
         const Field &f = F.f;
-        const int Ay = (f.n[1] - 1) / 8 + 1, Ax = (f.n[2] - 1) / 8 + 1;
         Cursor nx = cu;
         const bool has_next = cursor_next<MULTI>(nx, bv);
         Slab sn = sl;
         if (has_next) slab_of<MULTI>(sn, nx, bv);
         if (threadIdx.x == 0 && lv_field != fi) load_levels(lv, F.a.hdr);
         lv_field = fi;
+        uint16_t *land = land_of(buf);
 
-        // ---- landed codes -> code box; outliers' stored values and anchors -> value box
-        if (!wait_land(F.use_tma, bar, phase)) abort_flag = 1;
-        __syncthreads();  // copies visible; the previous slab's box writes are done
+        // ---- this slab's codes; the next slab's into the other buffer (its last reader,
+        // the slab before this one, is done: the loop ends with a barrier)
+        const bool landed = wait_land(F.use_tma, &bar[buf], phase[buf]);
+        if (!landed) abort_flag = 1;
+        pending_next = has_next && landed;
+        if (pending_next) {
+            const int nfi = MULTI ? nx.fi : 0;
+            const DField &N = B.fld[nfi];
+            issue_land<uint16_t, KP, EZ, 0>(land_of(buf ^ 1), N.a.codes, &B.map[nfi], N.use_tma, &bar[buf ^ 1], N.f,
+                                            sn);
+        }
+        if (anc_ok) box[a_off] = anc;  // this slab's anchors, fetched a slab ago
+        if (has_next) {
+            const int nfi = MULTI ? nx.fi : 0;
+            anc_ok = anchor_fetch(B.fld[nfi], sn, anc);
+        }
+        __syncthreads();  // landed codes visible (cp.async: every thread's copies waited for)
+        // ---- outliers (code 0): their stored values, scattered into xrec, go into the box
         {
             const int pz0 = sl.carried ? 1 : 0;
             const int nzp = min(EZ, f.n[0] - sl.g0[0]);
@@ -1050,69 +1183,67 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
             for (int i = threadIdx.x; i < nitem; i += NT) {
                 const int row = pz0 * EY + i / 5, q = i % 5;
                 const uint4 v = *reinterpret_cast<const uint4 *>(land + row * KP + 8 * q);
-                uint32_t *d = reinterpret_cast<uint32_t *>(cbox + row * CP + 8 * q);
-                d[0] = v.x;
-                if (q < 4) {
-                    d[1] = v.y;
-                    d[2] = v.z;
-                    d[3] = v.w;
-                }
-                // code 0 marks an outlier: its stored value was scattered into xrec
                 const uint32_t z = q < 4 ? (has_zero_half(v.x) | has_zero_half(v.y) | has_zero_half(v.z) |
                                             has_zero_half(v.w))
                                          : has_zero_half(v.x);  // the last group holds x = 32, 33 only
-                const int pz = row / EY, y = row % EY;
-                if (z && pz < nzp && y < nyr) {
-                    const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-                    for (int j = 0; j < 8 && 8 * q + j < min(nxc, EX); ++j) {
-                        if (((wv[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) {
-                            const size_t g = ((size_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * f.n[2] + sl.g0[2] +
-                                             8 * q + j;
-                            box[row * EX + 8 * q + j] = __ldg(F.a.xrec + g);
+                if (z) {
+                    const int pz = row / EY, y = row % EY;
+                    if (pz < nzp && y < nyr) {
+                        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+                        for (int j = 0; j < 8 && 8 * q + j < min(nxc, EX); ++j) {
+                            if (((wv[j >> 1] >> (16 * (j & 1))) & 0xffffu) == 0u) {
+                                const size_t g = ((size_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * f.n[2] +
+                                                 sl.g0[2] + 8 * q + j;
+                                box[row * EX + 8 * q + j] = __ldg(F.a.xrec + g);
+                            }
                         }
                     }
                 }
             }
-            // anchors of planes 8 and, when not carried, 0
-            constexpr int AYN = OY / 8 + 1, AXN = OX / 8 + 1;  // anchor rows / columns of the box
-            for (int i = threadIdx.x; i < 2 * AYN * AXN; i += NT) {
-                const int az = i / (AYN * AXN), ay = (i / AXN) % AYN, ax = i % AXN;
-                const int pz = 8 * az, y = 8 * ay, x = 8 * ax;
-                if ((az == 0 && sl.carried) || pz >= nzp || y >= nyr || x >= nxc) continue;
-                const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gxx = sl.g0[2] + x;
-                box[pz * PLANE + y * EX + x] = __ldg(F.a.anchors + ((size_t)(gz / 8) * Ay + gy / 8) * Ax + gxx / 8);
-            }
         }
-        __syncthreads();  // code box, anchors and levels ready, landing buffer free
+        __syncthreads();  // outlier values, anchors and levels ready
         if (abort_flag) break;
-        if (has_next) {
-            const int nfi = MULTI ? nx.fi : 0;
-            const DField &N = B.fld[nfi];
-            issue_land<uint16_t, KP, EZ, 0>(land, N.a.codes, &B.map[nfi], N.use_tma, bar, N.f, sn);
-        }
 
-        run_slab<false, false>(box, sk, sl, f, lv);  // ends with a barrier
+        const Sink sk{nullptr, land, nullptr, nullptr};
+        run_slab<false>(box, sk, sl, f, lv);  // ends with a barrier
 
-        // ---- write the owned planes: 8 lanes x 4 values per row, 4 rows per warp
+        // ---- write the owned planes
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int nzp = min(EZ, f.n[0] - sl.g0[0]);
         const int hi = min(sl.own_hi, nzp - 1);
         const int rows = (hi - sl.own_lo + 1) * OY;
-        const int sub = lane & 7;
-        const bool vec_x = F.a.vec_xrec;
-        for (int base = warp * 4; base < rows; base += NWARP * 4) {
-            const int row = base + (lane >> 3);
-            const int pz = sl.own_lo + row / OY, y = row % OY;
-            const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gx = sl.g0[2] + 4 * sub;
-            if (gy >= f.n[1] || gx >= f.n[2]) continue;
-            const float *s4 = box + pz * PLANE + y * EX + 4 * sub;
-            float *dst = F.a.xrec + ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
-            if (vec_x && gx + 3 < f.n[2]) {
-                *reinterpret_cast<float4 *>(dst) = make_float4(s4[0], s4[1], s4[2], s4[3]);
-            } else {
-                for (int j = 0; j < 4 && gx + j < f.n[2]; ++j) dst[j] = s4[j];
+        if (F.a.vec_xrec && sl.g0[1] + OY <= f.n[1] && sl.g0[2] + OX <= f.n[2]) {
+            // whole rows, 16-byte aligned: 8 values per thread, three planes per step
+            constexpr int PSTEP = NT / 4 / OY;
+            const int sub4 = threadIdx.x & 3;
+            int r = threadIdx.x >> 2;
+            const int y = r % OY;
+            const int pz = sl.own_lo + r / OY;
+            const size_t plane = (size_t)f.n[1] * f.n[2];
+            const float *sp = box + pz * PLANE + y * EX + 8 * sub4;
+            float *gp = F.a.xrec + ((size_t)(sl.g0[0] + pz) * f.n[1] + sl.g0[1] + y) * f.n[2] + sl.g0[2] + 8 * sub4;
+            for (; r < rows; r += NT / 4, sp += PSTEP * PLANE, gp += PSTEP * plane) {
+                reinterpret_cast<float4 *>(gp)[0] = make_float4(sp[0], sp[1], sp[2], sp[3]);
+                reinterpret_cast<float4 *>(gp)[1] = make_float4(sp[4], sp[5], sp[6], sp[7]);
+            }
+        } else {
+            // 8 lanes x 4 values per row, 4 rows per warp
+            const int sub = lane & 7;
+            for (int base = warp * 4; base < rows; base += NWARP * 4) {
+                const int row = base + (lane >> 3);
+                const int pz = sl.own_lo + row / OY, y = row % OY;
+                const int gz = sl.g0[0] + pz, gy = sl.g0[1] + y, gx = sl.g0[2] + 4 * sub;
+                if (gy >= f.n[1] || gx >= f.n[2]) continue;
+                const float *s4 = box + pz * PLANE + y * EX + 4 * sub;
+                float *dst = F.a.xrec + ((size_t)gz * f.n[1] + gy) * f.n[2] + gx;
+                if (F.a.vec_xrec && gx + 3 < f.n[2]) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(s4[0], s4[1], s4[2], s4[3]);
+                } else {
+                    for (int j = 0; j < 4 && gx + j < f.n[2]; ++j) dst[j] = s4[j];
+                }
             }
         }
-        __syncthreads();  // every thread is done reading the box
+        __syncthreads();  // every thread is done reading the box and this slab's codes
         if (!has_next) break;
         // ---- carry plane 8 into plane 0 of the next slab of the same run
         if (nx.item == cu.item) {
@@ -1121,15 +1252,23 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
         }
         cu = nx;
         sl = sn;
+        buf ^= 1;
     }
-    if (abort_flag && threadIdx.x == 0)
+    if (abort_flag && threadIdx.x == 0) {
         atomicOr(&const_cast<interp_header *>(B.fld[MULTI ? cu.fi : 0].a.hdr)->status, INTERP_STATUS_TIMEOUT);
+        // give the transfers still in flight (this slab's, and the next one's if it was
+        // issued) a second bounded wait before the CTA's shared memory is released
+        if (B.fld[MULTI ? cu.fi : 0].use_tma) {
+            mbar_wait_bounded(&bar[buf], phase[buf] ^ 1u, kTmaPolls);
+            if (pending_next) mbar_wait_bounded(&bar[buf ^ 1], phase[buf ^ 1], kTmaPolls);
+        }
+    }
     cp_async_wait_all();
 }
 
 // ------------------------------------------------------------ host side
 constexpr int kMaxDevices = 64;
-int compress_grid[4][kMaxDevices];  // [MULTI + 2 XDOM]
+int compress_grid[2][kMaxDevices];  // [MULTI]
 int decompress_grid[kMaxDevices], decompress_grid_multi[kMaxDevices];
 
 // Opt in to the kernel's dynamic shared memory and size the persistent grid
@@ -1211,11 +1350,8 @@ cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t 
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     int grid = 0;
-    bool xdom = false;
-    for (int i = 0; i < n; ++i) xdom = xdom || args[i].xdom32;
-    auto kernel = n > 1 ? (xdom ? k_compress<true, true> : k_compress<true, false>)
-                        : (xdom ? k_compress<false, true> : k_compress<false, false>);
-    cudaError_t e = prepare(kernel, kCompressSmem, compress_grid[(n > 1 ? 1 : 0) + (xdom ? 2 : 0)], grid);
+    auto kernel = n > 1 ? k_compress<true> : k_compress<false>;
+    cudaError_t e = prepare(kernel, kCompressSmem, compress_grid[n > 1 ? 1 : 0], grid);
     if (e != cudaSuccess) return e;
     thread_local CBatch B;  // large parameter block, filled on the host
     std::memset(&B, 0, sizeof(B));

@@ -20,7 +20,7 @@
  * nothing is interpolated along them.  level_kind has three entries; levels
  * coarser than stride 4 follow level_kind[2].
  *
- * Readings of the paper taken here (each is also listed in the design doc):
+ * Readings of the paper taken here:
  *   - neighbour domain is the closed 8^3 chunk [8*floor(n/8), min(.+8, n_d-1)]
  *     along the interpolation axis (Sec. IV-A, Fig. 3); optionally, along x, the
  *     closed 32-point block [32*floor(n/32), min(.+32, n_x-1)] of the GPU
@@ -28,7 +28,9 @@
  *     along x).  Anchors stay on the stride-8 grid either way;
  *   - the axis processed later in a level covers the whole finer grid (Fig. 3);
  *   - reconstruction from the integer code: x' = p + (float)(code - R) * 2e;
- *   - natural cubic uses the float nearest 1/40 as a multiplier.
+ *   - the cubic splines divide their integer-weighted sums by the printed
+ *     denominators: 16 for not-a-knot (a power of two, so the same as a
+ *     multiply by 0.0625) and 40 for the natural cubic (an IEEE division).
  */
 #include <math.h>
 #include <stdint.h>
@@ -122,7 +124,7 @@ float orc_spline(int kind, float m3, float m1, float p1, float p3)
     case K_QUAD_LEFT:     return ((6.0f * m1 - m3) + 3.0f * p1) * 0.125f;   /* -1/8, 6/8, 3/8 */
     case K_QUAD_RIGHT:    return ((3.0f * m1 + 6.0f * p1) - p3) * 0.125f;   /* 3/8, 6/8, -1/8 */
     case K_CUBIC_NAK:     return (9.0f * (m1 + p1) - (m3 + p3)) * 0.0625f;  /* -1, 9, 9, -1 over 16 */
-    case K_CUBIC_NATURAL: return (23.0f * (m1 + p1) - 3.0f * (m3 + p3)) * 0.025f; /* -3, 23, 23, -3 over 40 */
+    case K_CUBIC_NATURAL: return (23.0f * (m1 + p1) - 3.0f * (m3 + p3)) / 40.0f; /* -3, 23, 23, -3 over 40 */
     default:              return NAN;
     }
 }

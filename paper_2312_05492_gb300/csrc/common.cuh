@@ -62,18 +62,59 @@ __device__ __forceinline__ float sp_quad_right(float m1, float p1, float p3)
 {
     return ((3.0f * m1 + 6.0f * p1) - p3) * 0.125f;
 }
-// cubic with runtime coefficients: not-a-knot (9, 1, 1/16) or natural (23, 3, 1/40);
-// multiplying by 1 is exact, so the not-a-knot form is (9(m1+p1) - (m3+p3)) / 16.
-struct Cubic {
-    float a, b, c;
-};
-__device__ __forceinline__ Cubic cubic_coeffs(int natural)
+// Cubic splines: the integer-weighted sum over the printed denominator, i.e.
+// not-a-knot (9(m1+p1) - (m3+p3)) / 16, a multiply by 0.0625 (exact: a power of
+// two), and natural (23(m1+p1) - 3(m3+p3)) / 40, an IEEE division.
+__device__ __forceinline__ float sp_cubic_nak(float m3, float m1, float p1, float p3)
 {
-    return natural ? Cubic{23.0f, 3.0f, 0.025f} : Cubic{9.0f, 1.0f, 0.0625f};
+    return (9.0f * (m1 + p1) - (m3 + p3)) * 0.0625f;
 }
+// n / 40 rounded to nearest even, exactly as an IEEE division would give it.
+// Normal range: q = n * RN(1/40) is within one ulp of n / 40, the residual
+// n - 40 q is exact as one fused multiply-add, and q + residual * RN(1/40) is
+// the correctly rounded quotient (Markstein's correction step, P. Markstein,
+// IBM J. Res. Dev. 34(1), 1990).  Tiny numerators are scaled by 2^64 first
+// (the scaled quotient is normal and scaling back is exact while n / 40 stays
+// normal); numerators whose quotient is subnormal are divided in integers, in
+// units of 2^-149, with the remainder deciding the rounding.  Checked against
+// CUDA's IEEE division on every float input.
+__device__ __forceinline__ float div40_markstein(float n)
+{
+    const float y = 0.025f;  // RN(1/40)
+    const float q = __fmul_rn(n, y);
+    const float r = __fmaf_rn(-q, 40.0f, n);
+    return __fmaf_rn(r, y, q);
+}
+__device__ __forceinline__ float div40_tiny(float n)
+{
+    const float a = fabsf(n);
+    if (!(a <= 3.402823466e38f)) return __fmul_rn(n, 0.025f);  // inf / 40 = inf; NaN stays NaN
+    if (a >= 4.70197740e-37f)  // 40 * 2^-126: the quotient is normal
+        return __fmul_rn(div40_markstein(__fmul_rn(n, 18446744073709551616.0f)), 5.42101086e-20f);  // 2^64, 2^-64
+    // quotient below 2^-126: |n| = M * 2^-149 with M < 2^29, the result is round(M / 40) * 2^-149
+    const uint32_t M = (uint32_t)__fmul_rn(__fmul_rn(a, 1.26765060e30f), 5.62949953e14f);  // * 2^100 * 2^49: exact
+    uint32_t qi = M / 40u;
+    const uint32_t rem = M - 40u * qi;
+    if (rem > 20u || (rem == 20u && (qi & 1u))) ++qi;
+    return __uint_as_float((__float_as_uint(n) & 0x80000000u) | qi);
+}
+__device__ __forceinline__ float div40_rn(float n)
+{
+    const float a = fabsf(n);
+    return (a >= 8.07793567e-28f && a <= 3.402823466e38f) ? div40_markstein(n) : div40_tiny(n);  // 2^-90 .. max
+}
+__device__ __forceinline__ float sp_cubic_nat(float m3, float m1, float p1, float p3)
+{
+    return div40_rn(23.0f * (m1 + p1) - 3.0f * (m3 + p3));
+}
+// the cubic kind chosen at run time (0 = not-a-knot, 1 = natural)
+struct Cubic {
+    int natural;
+};
+__device__ __forceinline__ Cubic cubic_coeffs(int natural) { return Cubic{natural ? 1 : 0}; }
 __device__ __forceinline__ float sp_cubic(const Cubic &k, float m3, float m1, float p1, float p3)
 {
-    return (k.a * (m1 + p1) - k.b * (m3 + p3)) * k.c;
+    return k.natural ? sp_cubic_nat(m3, m1, p1, p3) : sp_cubic_nak(m3, m1, p1, p3);
 }
 
 // Level-wise quantization constants, read once per CTA from the header.

@@ -143,7 +143,7 @@ struct Levels {
     int ord_id;         // index of the axis order (ord_axis)
     // the same values packed for single 16-byte loads in the fixed-geometry passes
     float4 q4[3];       // per level: e, 2e, 1/(2e), spline (0 or 1)
-    float4 cub4[3];     // per axis: cubic coefficients a, b, c
+    int natural[3];     // per axis: natural cubic (else not-a-knot)
     uint4 k4;           // R, float(R) bits, cbias
 };
 
@@ -172,7 +172,7 @@ __device__ __forceinline__ void load_levels(Levels &lv, const interp_header *h)
     lv.xdom32 = h->cfg.domain_x == 32;
     for (int l = 0; l < 3; ++l) {
         lv.q4[l] = make_float4(lv.L[l].e, lv.L[l].twoe, lv.L[l].inv2e, lv.spline[l] ? 1.0f : 0.0f);
-        lv.cub4[l] = make_float4(lv.cub[l].a, lv.cub[l].b, lv.cub[l].c, 0.0f);
+        lv.natural[l] = lv.cub[l].natural;
     }
     lv.k4 = make_uint4((uint32_t)lv.R, __float_as_uint(lv.Rf), lv.cbias, 0u);
     // segment counts of every pass (the same rule as run_pass), so that threads
@@ -483,13 +483,23 @@ __device__ __forceinline__ void seg_apply(float *L, int ob, float p, uint32_t co
     if (code) L[ob] = xq;
 }
 
-// A segment of a full chunk: the fixed stencils of Fig. 3 (SPLINE: cubic at
+// Prediction kinds of the fixed-geometry passes: linear only, or splines by
+// neighbour count with the not-a-knot or the natural cubic.
+enum { KIND_LINEAR = 0, KIND_NAK = 1, KIND_NATURAL = 2 };
+template <int KIND>
+__device__ __forceinline__ float cubic_of(float m3, float m1, float p1, float p3)
+{
+    return KIND == KIND_NATURAL ? sp_cubic_nat(m3, m1, p1, p3) : sp_cubic_nak(m3, m1, p1, p3);
+}
+
+// A segment of a full chunk: the fixed stencils of Fig. 3 (splines: cubic at
 // offsets 3 and 5, quadratics at 1 and 7 for stride 1; quadratics at stride 2;
 // stride 4 is always linear).
-template <bool COMPRESS, int S, int BD, int KD, bool SPLINE>
-__device__ __forceinline__ void seg_full(float *L, uint16_t *C, const LevelQ &Lq, const Cubic &cub, uint32_t cbias,
-                                         float Rf, const SegOut &so)
+template <bool COMPRESS, int S, int BD, int KD, int KIND>
+__device__ __forceinline__ void seg_full(float *L, uint16_t *C, const LevelQ &Lq, uint32_t cbias, float Rf,
+                                         const SegOut &so)
 {
+    constexpr bool SPLINE = KIND != KIND_LINEAR;
     if (!COMPRESS && BD == 1 && KD == 1) {
         // decompression along x: the chunk row's 8 codes are one aligned 16-byte word
         // of the landed codes (rows of 80 bytes), so one load serves the segment
@@ -503,8 +513,8 @@ __device__ __forceinline__ void seg_full(float *L, uint16_t *C, const LevelQ &Lq
         } else {
             const float k0 = L[0], k2 = L[2], k4 = L[4], k6 = L[6], k8 = L[8];
             seg_apply(L, 1, SPLINE ? sp_quad_right(k0, k2, k4) : sp_linear(k0, k2), w.x >> 16, Lq, cbias);
-            seg_apply(L, 3, SPLINE ? sp_cubic(cub, k0, k2, k4, k6) : sp_linear(k2, k4), w.y >> 16, Lq, cbias);
-            seg_apply(L, 5, SPLINE ? sp_cubic(cub, k2, k4, k6, k8) : sp_linear(k4, k6), w.z >> 16, Lq, cbias);
+            seg_apply(L, 3, SPLINE ? cubic_of<KIND>(k0, k2, k4, k6) : sp_linear(k2, k4), w.y >> 16, Lq, cbias);
+            seg_apply(L, 5, SPLINE ? cubic_of<KIND>(k2, k4, k6, k8) : sp_linear(k4, k6), w.z >> 16, Lq, cbias);
             seg_apply(L, 7, SPLINE ? sp_quad_left(k4, k6, k8) : sp_linear(k6, k8), w.w >> 16, Lq, cbias);
         }
         return;
@@ -521,9 +531,9 @@ __device__ __forceinline__ void seg_full(float *L, uint16_t *C, const LevelQ &Lq
         const float k0 = L[0], k2 = L[2 * BD], k4 = L[4 * BD], k6 = L[6 * BD], k8 = L[8 * BD];
         seg_emit<COMPRESS>(L, C, BD, KD, SPLINE ? sp_quad_right(k0, k2, k4) : sp_linear(k0, k2), Lq, cbias, Rf,
                            so);
-        seg_emit<COMPRESS>(L, C, 3 * BD, 3 * KD, SPLINE ? sp_cubic(cub, k0, k2, k4, k6) : sp_linear(k2, k4), Lq,
+        seg_emit<COMPRESS>(L, C, 3 * BD, 3 * KD, SPLINE ? cubic_of<KIND>(k0, k2, k4, k6) : sp_linear(k2, k4), Lq,
                            cbias, Rf, so);
-        seg_emit<COMPRESS>(L, C, 5 * BD, 5 * KD, SPLINE ? sp_cubic(cub, k2, k4, k6, k8) : sp_linear(k4, k6), Lq,
+        seg_emit<COMPRESS>(L, C, 5 * BD, 5 * KD, SPLINE ? cubic_of<KIND>(k2, k4, k6, k8) : sp_linear(k4, k6), Lq,
                            cbias, Rf, so);
         seg_emit<COMPRESS>(L, C, 7 * BD, 7 * KD, SPLINE ? sp_quad_left(k4, k6, k8) : sp_linear(k6, k8), Lq, cbias,
                            Rf, so);
@@ -561,7 +571,6 @@ __device__ __forceinline__ void seg_trunc(float *L, uint16_t *C, int hi, bool sp
 // Constants of one fixed-geometry pass.
 struct PassK {
     LevelQ Lq;
-    Cubic cub;
     uint32_t cbias;
     float Rf;
     uint32_t R;
@@ -570,9 +579,10 @@ struct PassK {
 // Pass k of the level of stride S for axis order ORD.  Segments are numbered with
 // U (the faster other axis) fastest, then V, then the chunk along D; thread t
 // takes segments t, t + NT, ...  Threads without a segment skip the pass at once.
-template <bool COMPRESS, int ORD, bool CARRIED, int S, int K, bool SPLINE>
+template <bool COMPRESS, int ORD, bool CARRIED, int S, int K, int KIND>
 __device__ __forceinline__ void fast_pass(const FastCtx &c, const PassK &pk)
 {
+    constexpr bool SPLINE = KIND != KIND_LINEAR;
     constexpr int D = ord_axis(ORD, K);
     constexpr int U = axis_u(D), V = axis_v(D);
     constexpr int stepU = ord_rank(ORD, U) < K ? S : 2 * S;
@@ -588,11 +598,7 @@ __device__ __forceinline__ void fast_pass(const FastCtx &c, const PassK &pk)
                   KV = COMPRESS ? cstride(V) : lstride(V);
     // after the last pass of compression only plane 8 (carried to the next slab) is read again
     constexpr bool LAST = COMPRESS && S == 1 && K == 2;
-    Cubic cub = pk.cub;
-    if (S == 1 && SPLINE) {  // the pass axis's cubic
-        const float4 k = g_lv.cub4[D];
-        cub = Cubic{k.x, k.y, k.z};
-    }
+    const Cubic cub{KIND == KIND_NATURAL ? 1 : 0};  // truncated chunks choose per point
     SegOut so;
     so.hist = c.hist;
     so.spare = c.hist + HIST_SMEM_BINS + (threadIdx.x & 31);
@@ -608,7 +614,7 @@ __device__ __forceinline__ void fast_pass(const FastCtx &c, const PassK &pk)
         uint16_t *C = c.codes + v * KV + u * KU + 8 * cd * KD;
         so.keep = !LAST || (D != 0 && v == 8);
         so.owned = u < c.lim[U] && v < c.lim[V];
-        if (cd < c.nfull[D]) seg_full<COMPRESS, S, BD, KD, SPLINE>(L, C, pk.Lq, cub, pk.cbias, pk.Rf, so);
+        if (cd < c.nfull[D]) seg_full<COMPRESS, S, BD, KD, KIND>(L, C, pk.Lq, pk.cbias, pk.Rf, so);
         else seg_trunc<COMPRESS, S, BD, KD>(L, C, c.rem[D] - 8 * cd, SPLINE, pk.Lq, cub, pk.cbias, pk.Rf, so);
     }
 }
@@ -621,8 +627,10 @@ __device__ __forceinline__ void fast_pass_any(const FastCtx &c, const PassK &pk,
     constexpr int nU = count_on(ext_of(U), ord_rank(ORD, U) < K ? S : 2 * S);
     constexpr int nV = count_on(ext_of(V), ord_rank(ORD, V) < K ? S : 2 * S) - ((V == 0 && CARRIED) ? 1 : 0);
     if ((int)threadIdx.x < nU * nV * chunks_of(D)) {
-        if (spline) fast_pass<COMPRESS, ORD, CARRIED, S, K, true>(c, pk);
-        else fast_pass<COMPRESS, ORD, CARRIED, S, K, false>(c, pk);
+        // only stride 1 has four-neighbour (cubic) stencils inside a chunk
+        if (!spline) fast_pass<COMPRESS, ORD, CARRIED, S, K, KIND_LINEAR>(c, pk);
+        else if (S == 1 && g_lv.natural[D]) fast_pass<COMPRESS, ORD, CARRIED, S, K, KIND_NATURAL>(c, pk);
+        else fast_pass<COMPRESS, ORD, CARRIED, S, K, KIND_NAK>(c, pk);
     }
     __syncthreads();
 }
@@ -677,7 +685,6 @@ __device__ __forceinline__ void fast_levels(float *box, uint16_t *codes, uint32_
     pk.R = k.x;
     pk.Rf = __uint_as_float(k.y);
     pk.cbias = k.z;
-    pk.cub = Cubic{0.0f, 0.0f, 0.0f};
     switch (lv.ord_id) {
     case 0: fast_slab<COMPRESS, 0>(c, pk, carried); break;
     case 1: fast_slab<COMPRESS, 1>(c, pk, carried); break;

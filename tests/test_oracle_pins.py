@@ -88,6 +88,36 @@ def test_natural_cubic_weights_match_natural_spline():
         assert O.spline(O.K_CUBIC_NAK, *args) == pytest.approx(w_nak, abs=1e-7)
 
 
+def _round_f32(fr) -> float:
+    """The float32 nearest the rational fr, ties to even (exact rationals; no float
+    division involved)."""
+    from fractions import Fraction
+    f = np.float32(float(fr))
+    lo = f if Fraction(float(f)) <= fr else np.nextafter(f, np.float32(-np.inf))
+    hi = np.nextafter(lo, np.float32(np.inf))
+    dlo, dhi = fr - Fraction(float(lo)), Fraction(float(hi)) - fr
+    if dlo != dhi:
+        return float(lo if dlo < dhi else hi)
+    return float(lo if (int(np.asarray(lo).view(np.uint32)) & 1) == 0 else hi)
+
+
+def test_natural_cubic_divides_by_40():
+    """Sec. IV-B.1 prints the natural cubic as the sum -3x_{-3} + 23x_{-1} + 23x_{1}
+    - 3x_{3} over 40.  With integer neighbours the weighted sum N is exact in float32,
+    so the prediction must be N/40 rounded once to the nearest float32 (checked with
+    exact rationals).  A multiply by the float nearest 1/40 rounds twice and differs
+    from it on some of these sums; the test also checks that such sums were met."""
+    from fractions import Fraction
+    twice = 0
+    for b in range(1, 3000):
+        for c in (0, 1, 5, 11):
+            n = 46 * b - 6 * c  # m1 = p1 = b, m3 = p3 = c
+            want = _round_f32(Fraction(n, 40))
+            assert O.spline(O.K_CUBIC_NATURAL, c, b, b, c) == want, (b, c)
+            twice += float(np.float32(np.float32(n) * np.float32(0.025))) != want
+    assert twice > 0
+
+
 def test_polynomial_reproduction_exact_integer():
     """Exact reproduction on integer polynomials (all arithmetic exact in float32):
     NAK cubic for degree 3, quadratics for degree 2, linear and natural for degree 1;

@@ -266,10 +266,13 @@ int interp_quality_report(const uint32_t *d_hist, int32_t radius, const float *d
 /* Host only.  Code lengths and canonical codewords for the 2R symbols of h_hist (uint32
  * counts): Huffman's construction (the two lightest subtrees merge first; ties by weight,
  * then creation order: symbols by index, merged subtrees after), then, if a length
- * exceeds max_len (1..24), lengths above it are cut to max_len and the longest codewords
- * below it are lengthened until the Kraft sum is at most 1; canonical codewords assign
- * consecutive values in (length, symbol) order.  Unused symbols get length 0; a single
- * used symbol gets length 1.  h_lengths [2R] and h_codewords [2R] are outputs. */
+ * exceeds max_len (1..24), lengths above it are cut to max_len, then, while the Kraft
+ * sum exceeds 1, the codeword that is longest among those shorter than max_len gains one
+ * bit (on equal lengths the lighter symbol, on equal counts the higher index); canonical
+ * codewords assign consecutive values in (length, symbol) order.  Unused symbols get
+ * length 0; a single used symbol gets length 1.  h_lengths [2R] and h_codewords [2R] are
+ * outputs.  INTERP_EINVAL when more than 2^max_len symbols are used (no prefix code of
+ * max_len bits holds them). */
 int interp_huffman_codebook(const uint32_t *h_hist, int32_t radius, int32_t max_len, uint8_t *h_lengths,
                             uint32_t *h_codewords);
 

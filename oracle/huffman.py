@@ -45,6 +45,33 @@ def huffman_lengths(hist) -> np.ndarray:
     return lengths
 
 
+def limited_lengths(hist, max_len: int) -> np.ndarray:
+    """Huffman's lengths (huffman_lengths) limited to max_len bits.  The paper builds
+    the codebook on the host and names no limit; the reading taken here: when some
+    length exceeds max_len, every length above it is cut to max_len; then, while the
+    Kraft sum of the used symbols exceeds 1, the codeword that is longest among those
+    shorter than max_len is lengthened by one bit (on equal lengths the lighter
+    symbol, on equal weights the higher symbol index).  The Kraft sum is kept as an
+    exact rational."""
+    from fractions import Fraction
+    h = np.asarray(hist, dtype=np.int64).reshape(-1)
+    lengths = huffman_lengths(h)
+    used = [int(s) for s in np.flatnonzero(h)]
+    if not used or int(lengths.max()) <= max_len:
+        return lengths
+    if len(used) > (1 << max_len):
+        raise ValueError("more symbols than codewords of max_len bits")
+    for s in used:
+        lengths[s] = min(int(lengths[s]), max_len)
+    kraft = sum(Fraction(1, 1 << int(lengths[s])) for s in used)
+    while kraft > 1:
+        shorter = [s for s in used if lengths[s] < max_len]
+        s = max(shorter, key=lambda t: (int(lengths[t]), -int(h[t]), t))
+        kraft -= Fraction(1, 1 << (int(lengths[s]) + 1))
+        lengths[s] += 1
+    return lengths
+
+
 def kraft_sum(lengths) -> float:
     l = np.asarray(lengths)
     l = l[l > 0]

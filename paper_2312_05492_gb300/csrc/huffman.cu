@@ -517,6 +517,7 @@ bool huffman_codebook(const uint32_t *hist, int nsym, int max_len, uint8_t *leng
         if (hist[s]) used.push_back(s);
     }
     if (used.empty()) return true;
+    if (used.size() > (size_t(1) << max_len)) return false;  // no prefix code of max_len bits holds them
     std::vector<int> len(nsym, 0);
     if (used.size() == 1) {
         len[used[0]] = 1;

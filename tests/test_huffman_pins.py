@@ -62,3 +62,21 @@ def test_encode_decode_roundtrip_and_sizes():
         bits = int(l[codes[256 * k:256 * (k + 1)]].sum())
         assert offs[k + 1] - offs[k] == (bits + 31) // 32
     assert np.array_equal(H.decode_chunks(words, offs, codes.size, l, cw, chunk=256), codes)
+
+
+def test_length_limit_worked_example():
+    """Weights 1, 1, 2, 3, 5, 8: Huffman's lengths are 5, 5, 4, 3, 2, 1 (Kraft sum 1).
+    Limited to 3 bits: cut to 3, 3, 3, 3, 2, 1 (Kraft 5/4); lengthen the longest code
+    below 3 bits, symbol 4 (2 -> 3, Kraft 9/8); then symbol 5 (1 -> 2, Kraft 7/8)."""
+    hist = np.array([1, 1, 2, 3, 5, 8], np.uint32)
+    assert list(H.huffman_lengths(hist)) == [5, 5, 4, 3, 2, 1]
+    l = H.limited_lengths(hist, 3)
+    assert list(l) == [3, 3, 3, 3, 3, 2]
+    assert H.kraft_sum(l) == 0.875
+    assert list(H.limited_lengths(hist, 5)) == [5, 5, 4, 3, 2, 1]  # no length above the limit
+    # ties on length go to the lighter symbol: weights 5, 4, 2, 3, 1, 1, 1 have Huffman
+    # lengths 2, 2, 3, 3, 4, 4, 3; cut to 3 bits the Kraft sum is 9/8, and of the two
+    # 2-bit codes the lighter one (symbol 1) is lengthened, which makes it exactly 1
+    t = np.array([5, 4, 2, 3, 1, 1, 1], np.uint32)
+    assert list(H.huffman_lengths(t)) == [2, 2, 3, 3, 4, 4, 3]
+    assert list(H.limited_lengths(t, 3)) == [2, 3, 3, 3, 3, 3, 3]

@@ -540,3 +540,42 @@ def test_x_domain_32_roundtrip():
             cfg = _random_cfg(rng)
             cfg.domain_x = 32
             _check_roundtrip(x, cfg, float(10 ** rng.uniform(-4, -2)), "rel", rng)
+
+
+def _axis_field(shape, axis, g):
+    """A field equal to g(t) along `axis` and constant along the other two."""
+    t = np.arange(shape[axis], dtype=np.float64)
+    sh = [1, 1, 1]
+    sh[axis] = shape[axis]
+    return np.ascontiguousarray(np.broadcast_to(g(t).astype(np.float32).reshape(sh), shape))
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_profile_closed_forms(axis):
+    """Sec. IV-B.1 profiling on integer fields that vary along one axis (every stencil is
+    exact in float32).  Along an axis of 32 points the four sample coordinates are
+    12 + floor(7j/3) = 12, 14, 16, 19 (sum 61), each shared by 16 of the 64 samples.
+    Per-sample errors derived by hand at coordinate n:
+      g = 5t^3: not-a-knot 0 (it reproduces cubics); natural 3n (its weights map t^3 to
+      n^3 - 0.6n); stride-1 linear 15n; stride-2 linear 60n, counted twice (120n);
+      stride-2 quadratics 120 each side (the left one gives 5n^3 + 120, the right one
+      5n^3 - 120), 240 together;
+      g = 5t^2: 0, 1, 5, 2*20 = 40, 0.
+    Constant axes contribute 0 everywhere, and so do the three unused slots 3d + 2."""
+    shape = [20, 24, 28]
+    shape[axis] = 32
+    shape = tuple(shape)
+    want = np.zeros(18)
+    d = axis
+    p3 = O.profile(_axis_field(shape, axis, lambda t: 5 * t ** 3))
+    want[3 * d + 1], want[9 + d], want[12 + d], want[15 + d] = 16 * 3 * 61, 16 * 15 * 61, 16 * 120 * 61, 64 * 240
+    assert np.array_equal(p3, want), (p3, want)
+    p2 = O.profile(_axis_field(shape, axis, lambda t: 5 * t ** 2))
+    want[:] = 0
+    want[3 * d + 1], want[9 + d], want[12 + d] = 64 * 1, 64 * 5, 64 * 40
+    assert np.array_equal(p2, want), (p2, want)
+    # decision: not-a-knot (error 0) beats natural on the varying axis; every chosen
+    # cubic error is 0, so the axes keep their id order (ties); linear loses at both strides
+    cfg = O.autotune_decide(p3)
+    assert cfg.cubic_kind[axis] == 0 and tuple(cfg.order) == (0, 1, 2)
+    assert tuple(cfg.level_kind) == (1, 1, 1)

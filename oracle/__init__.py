@@ -27,12 +27,39 @@ K_ANCHOR, K_COPY, K_LINEAR, K_QUAD_LEFT, K_QUAD_RIGHT, K_CUBIC_NAK, K_CUBIC_NATU
 PROFILE_LEN = 18
 
 
+_libs = {}
+_threads = 1
+
+
+def set_threads(n: int) -> int:
+    """Run the oracle on n host threads (the OpenMP build, which splits the points of
+    each pass; its results are identical to the single-threaded build's), or on one
+    (the plain build) for n <= 1.  Returns the number of threads in use."""
+    global _lib, _threads
+    if n <= 1:
+        _lib, _threads = _open(False), 1
+    else:
+        _lib = _open(True)
+        _threads = int(_lib.orc_threads(int(n)))
+    return _threads
+
+
+def threads() -> int:
+    return _threads
+
+
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    path = library_path()
-    if not os.path.exists(path):
+    if _lib is None:
+        _lib = _open(False)
+    return _lib
+
+
+def _open(threaded: bool):
+    if threaded in _libs:
+        return _libs[threaded]
+    path = library_path(threaded)
+    if not os.path.exists(path) or not os.path.exists(library_path(not threaded)):
         _build()
     lib = ctypes.CDLL(path)
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
@@ -65,7 +92,9 @@ def _load():
     lib.orc_profile.argtypes = [P, i64, i64, i64, i32, P]
     lib.orc_autotune_decide.restype = None
     lib.orc_autotune_decide.argtypes = [P, P, P, P]
-    _lib = lib
+    lib.orc_threads.restype = ctypes.c_int
+    lib.orc_threads.argtypes = [ctypes.c_int]
+    _libs[threaded] = lib
     return lib
 
 

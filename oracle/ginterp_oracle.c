@@ -34,8 +34,24 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads of the OpenMP build (points of one pass in parallel); the plain build
+ * always runs on one.  Returns the number of threads that will be used. */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* stencil kinds (also the values of the kind map) */
 enum { K_ANCHOR = 0, K_COPY = 1, K_LINEAR = 2, K_QUAD_LEFT = 3, K_QUAD_RIGHT = 4,
@@ -237,6 +253,9 @@ int orc_schedule_maps(int64_t nz, int64_t ny, int64_t nx, const int32_t order[3]
     return 0;
 }
 
+/* A prediction read an undefined value (a broken schedule). */
+static void flag_bad(int *bad) { __atomic_store_n(bad, 1, __ATOMIC_RELAXED); }
+
 /* Prediction of point c (level l, axis d) from array v (reconstructed values,
  * or original values in the debug mode).  known (optional) flags which
  * entries of v are already defined; a read of an undefined entry sets *bad. */
@@ -251,18 +270,18 @@ static float predict_point(const sched_t *S, const float *v, const uint8_t *know
     int64_t im1 = i - s * stride_d, ip1 = i + s * stride_d;
     int64_t im3 = i - 3 * s * stride_d, ip3 = i + 3 * s * stride_d;
     m1 = v[im1];
-    if (known && !known[im1]) *bad = 1;
+    if (known && !known[im1]) flag_bad(bad);
     if (kind != K_COPY) {
         p1 = v[ip1];
-        if (known && !known[ip1]) *bad = 1;
+        if (known && !known[ip1]) flag_bad(bad);
     }
     if (kind == K_QUAD_LEFT || kind == K_CUBIC_NAK || kind == K_CUBIC_NATURAL) {
         m3 = v[im3];
-        if (known && !known[im3]) *bad = 1;
+        if (known && !known[im3]) flag_bad(bad);
     }
     if (kind == K_QUAD_RIGHT || kind == K_CUBIC_NAK || kind == K_CUBIC_NATURAL) {
         p3 = v[ip3];
-        if (known && !known[ip3]) *bad = 1;
+        if (known && !known[ip3]) flag_bad(bad);
     }
     *kind_out = kind;
     return orc_spline(kind, m3, m1, p1, p3);
@@ -285,11 +304,20 @@ static void for_each_in_pass(const sched_t *S, int l, int k, visit_fn fn, void *
         else if (j < k) { start[a] = 0; step[a] = s; }
         else { start[a] = 0; step[a] = 2 * s; }
     }
-    int64_t c[3];
-    for (c[0] = start[0]; c[0] < S->dims[0]; c[0] += step[0])
+    /* The points of one pass read only points of earlier passes and write only
+     * themselves, so the OpenMP build may split the outermost loop among threads
+     * (results identical to the single-threaded build). */
+    const int64_t n0 = S->dims[0] > start[0] ? (S->dims[0] - start[0] + step[0] - 1) / step[0] : 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i0 = 0; i0 < n0; ++i0) {
+        int64_t c[3];
+        c[0] = start[0] + i0 * step[0];
         for (c[1] = start[1]; c[1] < S->dims[1]; c[1] += step[1])
             for (c[2] = start[2]; c[2] < S->dims[2]; c[2] += step[2])
                 fn(ctx, c, d, l);
+    }
 }
 
 static void for_each_pass(const sched_t *S, visit_fn fn, void *ctx)

@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--shape", default=None, help="nz,ny,nx of a smaller field (profiling runs only)")
     p.add_argument("--ndim", type=int, default=3, choices=[1, 2, 3],
                    help="profiling runs of the 1-D / 2-D geometry on its 512 MiB field (64 x 2^21 / 32 x 2048^2)")
+    p.add_argument("--serve-requests", type=int, default=300,
+                   help="requests per load level of the serving extra in the default run")
     p.add_argument("--workload", default="field", choices=["field", "batch", "serve"],
                    help="field: the 512^3 round trip (default); batch: three uneven fields in one persistent "
                         "launch vs one call per field; serve: the continuous-batching serving loop")
@@ -310,6 +312,87 @@ def x_domain_variant(G, x, eb, cfg, dims, stream) -> dict:
     return out
 
 
+def field_variant(G, x, eb, cfg, stream, peak, what: str, capacity: int, k: int = 10) -> dict:
+    """One more configuration of the headline metric, outside the main timed region:
+    compress and decompress through the public API (device time per call, CUDA
+    events on the stream, k calls each after a warm-up), the tile kernels' own
+    times (library events) against the HBM roofline, the outlier count and whether
+    the first outlier buffer overflowed (the binding then retries with the exact
+    count), and the error bound."""
+    import torch
+    dims = tuple(x.shape)
+    n = x.numel()
+    first = G.compress(x, eb, cfg, capacity=capacity, grow_on_overflow=False)
+    h0 = first.host_header(refresh=True)
+    retried = bool(h0.status & G.STATUS_CAPACITY)
+    cap = int(h0.n_outliers) if retried else capacity
+    del first
+    bufs = G.allocate(dims, cfg, x.device, capacity=cap)
+    ws = torch.empty(G.interp_workspace_bytes(dims, cfg.to_c()), dtype=torch.uint8, device=x.device)
+    cf = G.CompressedField(dims, cfg, bufs["header"], bufs["anchors"], bufs["codes"], bufs["out_idx"],
+                           bufs["out_val"], bufs["hist"], bufs["capacity"])
+    xr = torch.empty_like(x)
+    for _ in range(3):
+        G.compress_into(x, eb, cfg, bufs, ws, stream)
+        G.decompress_into(cf, xr, stream)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    G.interp_timing_enable(True)
+    ms_c = timed(lambda: G.compress_into(x, eb, cfg, bufs, ws, stream))
+    ms_d = timed(lambda: G.decompress_into(cf, xr, stream))
+    G.interp_timing_enable(False)
+    cm, cn, dm, dn = G.interp_timing_read()
+    h = cf.host_header(refresh=True)
+    assert h.status == 0
+    err = float((xr - x).abs().max())
+    assert err <= level0_bound(h), (err, h.eb_abs)
+    A = cf.anchors.numel()
+    n_out = int(h.n_outliers)
+    c_alg, d_alg = 6 * n + 4 * A, 6 * n + 4 * A + 4 * n_out
+    c_tile, d_tile = cm / max(cn, 1), dm / max(dn, 1)
+    out = {"workload": what, "shape": list(dims), "eb_rel": eb, "eb_abs": h.eb_abs, "alpha": h.alpha,
+           "dim_order": list(h.cfg.dim_order), "level_kind": list(h.cfg.level_kind),
+           "cubic_kind": list(h.cfg.cubic_kind),
+           "compress_gbs": round(4 * n / (ms_c * 1e-3) / 1e9, 2),
+           "decompress_gbs": round(4 * n / (ms_d * 1e-3) / 1e9, 2),
+           "compress_ms": round(ms_c, 4), "decompress_ms": round(ms_d, 4),
+           "compress_tile_ms": round(c_tile, 5), "decompress_tile_ms": round(d_tile, 5),
+           "compress_tile_roofline_frac": round(c_alg / (c_tile * 1e-3) / 1e9 / peak, 4),
+           "decompress_tile_roofline_frac": round(d_alg / (d_tile * 1e-3) / 1e9 / peak, 4),
+           "n_outliers": n_out, "outlier_fraction": round(n_out / n, 6),
+           "first_capacity": capacity, "capacity_retry": retried,
+           "max_abs_err_over_eb": err / h.eb_abs, "steps": k}
+    del bufs, ws, cf, xr
+    torch.cuda.empty_cache()
+    return out
+
+
+def serve_extra(local: int, requests: int) -> dict:
+    """The continuous-batching serving loop against one call per request on the same
+    arrivals (Poisson, mixed compress/decompress), swept past the single-call
+    capacity; outside the main timed region."""
+    from types import SimpleNamespace
+
+    from paper_2312_05492_gb300 import serve
+    return serve.bench(SimpleNamespace(requests=requests, loads=(0.5, 1.0, 2.0, 3.0)), local)
+
+
+def batch_extra(args, local: int) -> dict:
+    """Three uneven fields in one persistent launch (eager and CUDA-graph replay)
+    against one call per field; outside the main timed region."""
+    from types import SimpleNamespace
+    return run_batch(SimpleNamespace(warmup=3, steps=20), 0, 1, local)
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -443,6 +526,11 @@ def run_ours(args, rank, world, local):
         out["x_extended_domain"] = x_domain_variant(G, x, args.eb, cfg, dims, stream)
         out["lossless"] = lossless_stage(G, cf, stream)
         out["nd_variants"] = [nd_variant(G, 2, args.eb, stream, peak), nd_variant(G, 1, args.eb, stream, peak)]
+        if args.shape == SHAPE and args.ndim == 3:
+            # the other configurations of the metric: rel 1e-4 on the same field, the
+            # 1024^3 outlier-heavy shock field at rel 1e-5, the batch and the serving loop
+            out["field_1e4"] = field_variant(G, x, 1e-4, cfg, stream, peak, WORKLOAD.replace("1e-3", "1e-4"),
+                                             capacity=n // 64)
 
     # ---- end to end through the public API with host buffers: every step copies its
     # field from pinned host memory, compresses, decompresses and copies the
@@ -505,9 +593,28 @@ def run_ours(args, rank, world, local):
                               "two slots overlap the copies of neighbouring steps with compute"}
         assert torch.equal(host_out[(k - 1) % 2].view(torch.int32), xrec.cpu().view(torch.int32))
 
-    # ---- CPU baseline: the oracle as it stands, single-threaded, rank 0 only
+    # ---- CPU baseline: the oracle as it stands, rank 0 only
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(x, args.eb, full=True)
+
+    # ---- the remaining configurations of the metric (untimed by the step loop)
+    if not args.no_extras and args.shape == SHAPE and args.ndim == 3 and world == 1:
+        del x, bufs, ws, cf, xrec
+        if not args.no_e2e:
+            del host_x, host_out, xd, xo, sb, sws, scf
+        torch.cuda.empty_cache()
+        x5 = fields.shocks((1024, 1024, 1024), 6, device=dev, fft_dtype=torch.float32)
+        torch.cuda.empty_cache()
+        cfg5 = G.Config(level_kind=(1, 1, 1), cubic_kind=(0, 0, 0), dim_order=(0, 1, 2), eb_mode="rel", radius=512)
+        out["field_1024"] = field_variant(G, x5, 1e-5, cfg5, stream, peak,
+                                          "1024^3 float32 GRF k^-3 + 8 planar steps of 10 std, seed 6, rel eb 1e-5, "
+                                          "spline levels, not-a-knot, order z-y-x", capacity=x5.numel() // 64, k=5)
+        del x5
+        torch.cuda.empty_cache()
+        out["batch"] = batch_extra(args, local)
+        torch.cuda.empty_cache()
+        out["serve"] = serve_extra(local, args.serve_requests)
+        torch.cuda.empty_cache()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

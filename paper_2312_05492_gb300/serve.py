@@ -36,6 +36,8 @@ class Request:
     kind: str               # "compress" | "decompress"
     edge: int = 0           # cube edge (compress)
     eb: float = 1e-3        # relative bound (compress)
+    base: int = 0           # which resident source field the request's cube comes from
+    offset: tuple = (0, 0, 0)  # the cube's corner in that field
     src: int = -1           # compress request whose result to decompress
     done: float = float("nan")
     nbytes: int = 0         # field bytes handled
@@ -60,21 +62,25 @@ def make_requests(n: int, rate_hz: float, seed: int = 5, min_edge: int = 32, max
             reqs.append(Request(i, t, "decompress", src=src))
         else:
             edge = int(round(math.exp(rng.uniform(math.log(min_edge), math.log(max_edge)))))
-            reqs.append(Request(i, t, "compress", edge=edge, eb=rng.choice(list(ebs))))
+            off = tuple(rng.randrange(max_edge - edge + 1) for _ in range(3))
+            reqs.append(Request(i, t, "compress", edge=edge, eb=rng.choice(list(ebs)), base=rng.randrange(2),
+                                offset=off))
             compressed.append(i)
     return reqs
 
 
 class FieldSource:
-    """Request inputs: cubes cut from one resident 512^3 GRF (k^-3); each request gets
-    its own contiguous copy (the request's payload arriving on the device)."""
+    """Request inputs: each compress request's cube is cut at its own offset from one
+    of two resident 512^3 GRFs (k^-3, seeds 0 and 1), as its own contiguous copy (the
+    request's payload arriving on the device), so requests carry distinct data."""
 
     def __init__(self, device, edge: int = 512, seed: int = 0):
         from . import fields
-        self.src = fields.grf((edge, edge, edge), 3.0, seed, device=device)
+        self.src = [fields.grf((edge, edge, edge), 3.0, seed + b, device=device) for b in range(2)]
 
-    def cube(self, edge: int) -> torch.Tensor:
-        return self.src[:edge, :edge, :edge].contiguous()
+    def cube(self, r: Request) -> torch.Tensor:
+        z, y, x = r.offset
+        return self.src[r.base % len(self.src)][z:z + r.edge, y:y + r.edge, x:x + r.edge].contiguous()
 
 
 def _capacity(r: Request) -> int:
@@ -82,8 +88,9 @@ def _capacity(r: Request) -> int:
 
 
 def _compress_bytes(n: int, capacity: int) -> int:
-    # input + codes + outlier buffers + workspace bound + small arrays
-    return 4 * n + 2 * n + capacity * 8 + n // 8 + (1 << 16)
+    # input + codes + outlier buffers + small arrays (workspaces come from the pool,
+    # charged once when the engine starts)
+    return 4 * n + 2 * n + capacity * 8 + (1 << 16)
 
 
 def _resident_bytes(cf: G.CompressedField) -> int:
@@ -92,35 +99,64 @@ def _resident_bytes(cf: G.CompressedField) -> int:
 
 class Engine:
     def __init__(self, device, budget_bytes: int = 40 << 30, streams: int = 2, source: FieldSource | None = None,
-                 keep_results: bool = False):
+                 keep_results: bool = False, max_edge: int = 512):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.used = 0
+        self.evicted = 0
         self.source = source or FieldSource(self.device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.resident: OrderedDict[int, Request] = OrderedDict()   # compressed results kept on device
         self.inflight: list[tuple] = []
-        self.ws_pool: dict = {}
         self.keep_results = keep_results
+        # one workspace per (stream, batch slot), sized once for the largest field and
+        # charged to the budget for the engine's lifetime
+        ws_bytes = self.workspace_bytes(max_edge)
+        self.ws_pool = {(si, k): torch.empty(ws_bytes, dtype=torch.uint8, device=self.device)
+                        for si in range(streams) for k in range(MAX_BATCH)}
+        self.pool = ws_bytes * len(self.ws_pool)
+        self.used += self.pool
+
+    @staticmethod
+    def workspace_bytes(max_edge: int) -> int:
+        return G.interp_workspace_bytes((max_edge,) * 3, G.Config(autotune=True, eb_mode="rel").to_c())
+
+    @classmethod
+    def pool_bytes(cls, streams: int, max_edge: int) -> int:
+        """Device memory the engine's workspace pool takes from its budget."""
+        return cls.workspace_bytes(max_edge) * streams * MAX_BATCH
 
     # ---------------------------------------------------------------- memory
-    def _reserve(self, nbytes: int) -> bool:
-        while self.used + nbytes > self.budget and self.resident:
-            _, old = self.resident.popitem(last=False)   # evict the oldest unconsumed result
+    def _reserve(self, nbytes: int, protected=frozenset()) -> bool:
+        """Reserve budget, evicting the oldest resident results if that makes room.
+        Nothing is evicted unless the eviction lets the reservation succeed, and a
+        result whose decompress request has already arrived (protected) is kept (only
+        the run loop's last resort, when nothing can run at all, frees one)."""
+        if self.used + nbytes <= self.budget:
+            self.used += nbytes
+            return True
+        need = self.used + nbytes - self.budget
+        victims, freed = [], 0
+        for rid, r in self.resident.items():   # oldest first
+            if rid in protected:
+                continue
+            victims.append(rid)
+            freed += _resident_bytes(r.result)
+            if freed >= need:
+                break
+        if freed < need:
+            return False
+        for rid in victims:
+            old = self.resident.pop(rid)
             self.used -= _resident_bytes(old.result)
             old.result = None
-        if self.used + nbytes > self.budget:
-            return False
+            self.evicted += 1
         self.used += nbytes
         return True
 
     def _workspace(self, dims, cfg, stream_idx: int, slot: int) -> torch.Tensor:
-        need = G.interp_workspace_bytes(dims, cfg.to_c())
-        key = (stream_idx, slot)
-        ws = self.ws_pool.get(key)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(max(need, 1 << 20), dtype=torch.uint8, device=self.device)
-            self.ws_pool[key] = ws
+        ws = self.ws_pool[(stream_idx, slot)]
+        assert ws.numel() >= G.interp_workspace_bytes(dims, cfg.to_c())
         return ws
 
     # ---------------------------------------------------------------- batches
@@ -132,7 +168,7 @@ class Engine:
             for r in batch:
                 if r.kind != "compress":
                     continue
-                x = self.source.cube(r.edge)
+                x = self.source.cube(r)
                 cfg = G.Config(autotune=True, eb_mode="rel", radius=512)
                 bufs = G.allocate(tuple(x.shape), cfg, self.device, capacity=_capacity(r))
                 ws = self._workspace(tuple(x.shape), cfg, stream_idx, slot)
@@ -208,6 +244,8 @@ class Engine:
         batch, rest, dropped = [], [], 0
         nc = nd = 0
         full = False
+        # results that an arrived decompress request waits for are never evicted
+        protected = frozenset(r.src for r in pending if r.kind == "decompress")
         for r in pending:
             if full:
                 rest.append(r)
@@ -227,19 +265,19 @@ class Engine:
                     full = True
                     continue
                 del self.resident[src.rid]        # consumed by this request: no longer evictable
-                if not self._reserve(4 * src.result.codes.numel()):
+                if not self._reserve(4 * src.result.codes.numel(), protected):
                     self.resident[src.rid] = src  # no room yet: keep it for a later batch
                     rest.append(r)
                     continue
                 nd += 1
             else:
                 need = _compress_bytes(r.edge ** 3, _capacity(r))
-                if need > self.budget:            # can never fit: reject instead of waiting forever
+                if need > self.budget - self.pool:  # can never fit: reject instead of waiting forever
                     r.done = t
                     r.failed = "larger than the memory budget"
                     dropped += 1
                     continue
-                if nc >= MAX_BATCH or not self._reserve(need):
+                if nc >= MAX_BATCH or not self._reserve(need, protected):
                     rest.append(r)
                     full = nc >= MAX_BATCH
                     continue
@@ -268,6 +306,15 @@ class Engine:
                 if batch:
                     self.launch(batch, si, reqs)
                     continue
+                if not self.inflight and self.resident:
+                    # nothing runs and nothing fits: the budget is held by results whose
+                    # decompress requests are waiting for room themselves.  Free the
+                    # oldest one (its request is dropped) so that the rest progress.
+                    _, old = self.resident.popitem(last=False)
+                    self.used -= _resident_bytes(old.result)
+                    old.result = None
+                    self.evicted += 1
+                    continue
             if not self.inflight and not pending and i < len(reqs):
                 time.sleep(max(0.0, min(1e-3, reqs[i].arrival - now())))
             elif self.inflight:
@@ -289,7 +336,7 @@ def run_fifo(reqs: list[Request], device, source: FieldSource, time_limit: float
         while now() < r.arrival:
             time.sleep(max(0.0, min(1e-3, r.arrival - now())))
         if r.kind == "compress":
-            x = source.cube(r.edge)
+            x = source.cube(r)
             cfg = G.Config(autotune=True, eb_mode="rel", radius=512)
             r.result = G.compress(x, r.eb, cfg, capacity=max(1024, x.numel() // 16), workspace=ws)
             r.nbytes = 4 * x.numel()
@@ -309,15 +356,19 @@ def run_fifo(reqs: list[Request], device, source: FieldSource, time_limit: float
 
 
 def summarize(reqs: list[Request]) -> dict:
+    """Latency percentiles and delivered GB/s over the served requests, with the
+    number of requests that could not be served (and why) beside them."""
     lat = sorted((r.done - r.arrival) for r in reqs if not math.isnan(r.done) and not r.failed)
     if not lat:
-        return {"completed": 0}
+        return {"completed": 0, "failed": sum(1 for r in reqs if r.failed)}
     span = max(r.done for r in reqs if not math.isnan(r.done)) - min(r.arrival for r in reqs)
     byts = sum(r.nbytes for r in reqs if not math.isnan(r.done) and not r.failed)
     q = lambda p: lat[min(len(lat) - 1, int(p * (len(lat) - 1) + 0.5))]  # noqa: E731
     return {"completed": len(lat), "p50_ms": round(1e3 * q(0.50), 3), "p99_ms": round(1e3 * q(0.99), 3),
             "mean_ms": round(1e3 * sum(lat) / len(lat), 3), "gbs": round(byts / span / 1e9, 2),
             "span_s": round(span, 3), "failed": sum(1 for r in reqs if r.failed),
+            "failed_source_evicted": sum(1 for r in reqs if r.failed == "source evicted"),
+            "unfinished": sum(1 for r in reqs if math.isnan(r.done)),
             "retried": sum(1 for r in reqs if r.retries)}
 
 
@@ -349,15 +400,31 @@ def bench(args, local: int) -> dict:
                       "requests": nreq, "hbm_budget_gb": 40, "streams": 2, "max_batch": MAX_BATCH,
                       "single_call_capacity_hz": round(cap, 1)},
            "loads": []}
-    for frac in (0.5, 1.0, 1.2):
+    loads = tuple(getattr(args, "loads", None) or (0.5, 1.0, 1.5, 2.0, 3.0))
+    for frac in loads:
         rate = frac * cap
         fifo = summarize(run_fifo(make_requests(nreq, rate), dev, source))
-        eng = summarize(Engine(dev, source=source).run(make_requests(nreq, rate)))
+        engine = Engine(dev, source=source)
+        eng = summarize(engine.run(make_requests(nreq, rate)))
+        eng["evicted_results"] = engine.evicted
         out["loads"].append({"load_of_single_capacity": frac, "rate_hz": round(rate, 1),
-                             "continuous_batching": eng, "one_call_per_request": fifo})
-    ref = out["loads"][1]["continuous_batching"]
+                             "continuous_batching": eng, "one_call_per_request": fifo,
+                             "gbs_ratio": round(eng.get("gbs", 0.0) / fifo["gbs"], 3) if fifo.get("gbs") else None})
+        del engine
+        torch.cuda.empty_cache()
+    ref = next((L for L in out["loads"] if L["load_of_single_capacity"] == 1.0), out["loads"][0])["continuous_batching"]
+    sat = out["loads"][-1]
     out["value"] = ref.get("p99_ms")
     out["p50_ms"] = ref.get("p50_ms")
     out["p99_ms"] = ref.get("p99_ms")
     out["gbs"] = ref.get("gbs")
+    out["failed"] = ref.get("failed")
+    out["saturated"] = {"load_of_single_capacity": sat["load_of_single_capacity"],
+                        "continuous_batching_gbs": sat["continuous_batching"].get("gbs"),
+                        "one_call_per_request_gbs": sat["one_call_per_request"].get("gbs"),
+                        "gbs_ratio": sat["gbs_ratio"],
+                        "continuous_batching_p50_ms": sat["continuous_batching"].get("p50_ms"),
+                        "continuous_batching_p99_ms": sat["continuous_batching"].get("p99_ms"),
+                        "one_call_per_request_p50_ms": sat["one_call_per_request"].get("p50_ms"),
+                        "one_call_per_request_p99_ms": sat["one_call_per_request"].get("p99_ms")}
     return out

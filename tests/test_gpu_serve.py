@@ -22,7 +22,7 @@ def source():
 
 def test_results_same_alone_and_in_the_mix(source):
     reqs = serve.make_requests(120, rate_hz=20000.0, seed=7, min_edge=16, max_edge=96)
-    eng = serve.Engine("cuda", source=source, keep_results=True)
+    eng = serve.Engine("cuda", source=source, keep_results=True, max_edge=96)
     eng.run(reqs, time_limit=60.0)
     assert all(not math.isnan(r.done) for r in reqs)
     batched = [r for r in reqs if r.kind == "compress"]
@@ -31,7 +31,7 @@ def test_results_same_alone_and_in_the_mix(source):
     ws = G.Workspace()
     for r in reqs:
         if r.kind == "compress":
-            x = source.cube(r.edge)
+            x = source.cube(r)
             alone = G.compress(x, r.eb, G.Config(autotune=True, eb_mode="rel", radius=512),
                                capacity=max(1024, x.numel() // 16), workspace=ws)
             cf = r.result
@@ -54,7 +54,7 @@ def test_continuous_batching_overlaps_requests(source):
     """A burst of simultaneous arrivals is served in few batched launches."""
     reqs = serve.make_requests(64, rate_hz=1e9, seed=9, min_edge=16, max_edge=64, decompress_frac=0.0)
     launched = []
-    eng = serve.Engine("cuda", source=source)
+    eng = serve.Engine("cuda", source=source, max_edge=96)
     orig = eng.launch
 
     def spy(batch, si, rr):
@@ -70,15 +70,40 @@ def test_continuous_batching_overlaps_requests(source):
 
 
 def test_budget_admission_evicts_oldest_results(source):
-    """With a small budget, compressed results that nobody consumed are evicted;
-    their decompress requests are dropped rather than served wrong data."""
-    reqs = serve.make_requests(60, rate_hz=1e9, seed=3, min_edge=32, max_edge=48)
-    eng = serve.Engine("cuda", source=source, budget_bytes=3 << 20)
+    """With a small budget, compressed results that nobody has asked for yet are
+    evicted to admit new work; their decompress requests, arriving later, are dropped
+    rather than served wrong data."""
+    comp = serve.make_requests(40, rate_hz=1e9, seed=3, min_edge=32, max_edge=48, decompress_frac=0.0)
+    late = [serve.Request(40 + i, 0.5, "decompress", src=i) for i in range(20)]
+    reqs = comp + late
+    pool = serve.Engine.pool_bytes(2, 48)  # the workspace pool counts against the budget
+    eng = serve.Engine("cuda", source=source, budget_bytes=pool + (3 << 20), max_edge=48)
     eng.run(reqs, time_limit=60.0)
     assert all(not math.isnan(r.done) for r in reqs)
     assert eng.used <= eng.budget
-    assert any(r.failed == "source evicted" for r in reqs)
+    assert any(r.failed == "source evicted" for r in reqs) and eng.evicted > 0
     # a request larger than the whole budget is rejected, not left waiting
     big = serve.make_requests(3, rate_hz=1e9, seed=1, min_edge=96, max_edge=96, decompress_frac=0.0)
-    serve.Engine("cuda", source=source, budget_bytes=1 << 20).run(big, time_limit=30.0)
+    pool = serve.Engine.pool_bytes(2, 96)
+    serve.Engine("cuda", source=source, budget_bytes=pool + (1 << 20), max_edge=96).run(big, time_limit=30.0)
     assert all(r.failed == "larger than the memory budget" for r in big)
+
+
+def test_eviction_only_when_it_makes_room(source):
+    """The reservation evicts nothing when evicting every evictable result would
+    still not make room, and never evicts a protected result."""
+    eng = serve.Engine("cuda", source=source, budget_bytes=serve.Engine.pool_bytes(2, 32) + (1 << 20), max_edge=32)
+    x = torch.zeros((32, 32, 32), device="cuda")
+    cfg = G.Config(autotune=False, eb_mode="abs", radius=512)
+    for rid in range(3):
+        r = serve.Request(rid, 0.0, "compress", edge=32)
+        r.result = G.compress(x, 1e-3, cfg, capacity=1024)
+        eng.resident[rid] = r
+        eng.used += serve._resident_bytes(r.result)
+    before = eng.used
+    assert not eng._reserve(eng.budget)           # more than the whole budget: nothing evicted
+    assert eng.used == before and len(eng.resident) == 3 and eng.evicted == 0
+    one = serve._resident_bytes(eng.resident[0].result)
+    room = eng.budget - eng.used
+    assert eng._reserve(room + one, protected=frozenset({0}))  # one eviction is enough: the oldest unprotected
+    assert list(eng.resident) == [0, 2] and eng.evicted == 1

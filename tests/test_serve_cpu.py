@@ -19,6 +19,9 @@ def test_request_stream_is_seeded_and_poisson():
     logs = [math.log(r.edge) for r in comp]                   # log-uniform edges
     assert abs(statistics.mean(logs) - 0.5 * (math.log(32) + math.log(512))) < 0.1
     assert {r.eb for r in comp} == {1e-2, 1e-3, 1e-4}
+    # every cube lies inside its 512^3 source field, at its own offset
+    assert all(0 <= o and o + r.edge <= 512 for r in comp for o in r.offset)
+    assert len({(r.base, r.offset) for r in comp}) > 0.9 * len(comp)
     seen = set()
     for r in a:                                               # decompress only earlier, unconsumed results
         if r.kind == "decompress":

@@ -156,6 +156,26 @@ size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg)
     return ws_layout(dims).total;
 }
 
+// The compression set-up of one field (zeroing, profile, range and bounds).
+gi::PrologueItem prologue_item(const interp_compress_item &it, const WsLayout &L)
+{
+    unsigned char *ws = static_cast<unsigned char *>(it.d_ws);
+    gi::PrologueItem p;
+    p.x = it.d_x;
+    p.d = to_dims(it.dims);
+    p.eb = it.eb;
+    p.cfg = it.cfg;
+    p.alpha = effective_alpha(it.cfg, it.eb);
+    p.hdr = it.d_hdr;
+    p.counter = reinterpret_cast<uint32_t *>(ws + L.ctrl);
+    p.ctrl_words = (int)(kCtrlBytes / sizeof(uint32_t));
+    p.partials = ws + L.partials;
+    p.blockcnt = reinterpret_cast<uint32_t *>(ws + L.blockcnt);
+    p.nblk = L.nblk;
+    p.hist = it.d_hist;
+    return p;
+}
+
 // One field in the 1-D or 2-D geometry: the same setup and compaction as the 3-D
 // path around the per-tile kernel of nd.cu.
 int compress_nd(const interp_compress_item &it, interp_stream_t stream)
@@ -174,17 +194,10 @@ int compress_nd(const interp_compress_item &it, interp_stream_t stream)
     unsigned int *counter = reinterpret_cast<unsigned int *>(ws + L.ctrl);
     uint32_t *bitmap = reinterpret_cast<uint32_t *>(ws + L.bitmap);
     uint32_t *blockcnt = reinterpret_cast<uint32_t *>(ws + L.blockcnt);
-    cudaError_t e = cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(blockcnt, 0, sizeof(uint32_t) * (size_t)L.nblk, s);
-    if (e == cudaSuccess && it.d_hist) e = cudaMemsetAsync(it.d_hist, 0, sizeof(uint32_t) * 2 * (size_t)c.radius, s);
-    if (e == cudaSuccess && c.autotune) e = gi::launch_profile(it.d_x, d, it.d_hdr, 1, s, c.ndim);
-    if (e == cudaSuccess) {
-        if (c.eb_mode)
-            e = gi::launch_range(it.d_x, d, it.eb, c, alpha, it.d_hdr, ws + L.partials, counter, gi::range_blocks(),
-                                 s);
-        else
-            e = gi::launch_header_init(it.d_hdr, d, it.eb, c, alpha, s);
-    }
+    (void)counter;
+    (void)alpha;
+    const gi::PrologueItem pro = prologue_item(it, L);
+    cudaError_t e = gi::launch_prologue(&pro, 1, s);
     const gi::CompressArgs args{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
                                 it.d_hdr, false, false, 1};
     if (e == cudaSuccess) {
@@ -192,9 +205,12 @@ int compress_nd(const interp_compress_item &it, interp_stream_t stream)
         e = gi::launch_nd_compress(c.ndim, args, s);
         timing_mark(0, 1, s);
     }
-    if (e == cudaSuccess)
-        e = gi::launch_outlier_compaction(bitmap, blockcnt, L.words, d, it.d_x, it.d_out_idx, it.d_out_val,
-                                          it.out_capacity, it.d_hdr, s, true);  // row-major bitmap (nd.cu)
+    if (e == cudaSuccess) {
+        // row-major bitmap (nd.cu); the 1-D / 2-D kernels count every bin themselves
+        const gi::CompactItem ci{bitmap, blockcnt, L.words, d, it.d_x, it.d_out_idx, it.d_out_val,
+                                 it.out_capacity, it.d_hdr, true, nullptr, c.radius};
+        e = gi::launch_outlier_compaction(&ci, 1, s);
+    }
     return cuda_status(e);
 }
 
@@ -213,42 +229,37 @@ int interp_compress_batched(const interp_compress_item *items, int n, interp_str
         if (it.ws_bytes < L[i].total) return INTERP_EWORKSPACE;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // set-up of every field in two launches (zeroing; profile, range and bounds)
     gi::CompressArgs args[gi::kMaxBatch];
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    gi::PrologueItem pro[gi::kMaxBatch];
+    for (int i = 0; i < n; ++i) {
         const interp_compress_item &it = items[i];
         const interp_config &c = it.cfg;
         const Dims d = to_dims(it.dims);
-        const double alpha = effective_alpha(c, it.eb);
         unsigned char *ws = static_cast<unsigned char *>(it.d_ws);
-        unsigned int *counter = reinterpret_cast<unsigned int *>(ws + L[i].ctrl);
         uint32_t *bitmap = reinterpret_cast<uint32_t *>(ws + L[i].bitmap);
         uint32_t *blockcnt = reinterpret_cast<uint32_t *>(ws + L[i].blockcnt);
-        e = cudaMemsetAsync(ws + L[i].ctrl, 0, kCtrlBytes, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(blockcnt, 0, sizeof(uint32_t) * (size_t)L[i].nblk, s);
-        if (e == cudaSuccess && it.d_hist)
-            e = cudaMemsetAsync(it.d_hist, 0, sizeof(uint32_t) * 2 * (size_t)c.radius, s);
-        if (e == cudaSuccess && c.autotune) e = gi::launch_profile(it.d_x, d, it.d_hdr, 1, s);
-        if (e == cudaSuccess) {
-            if (c.eb_mode)
-                e = gi::launch_range(it.d_x, d, it.eb, c, alpha, it.d_hdr, ws + L[i].partials, counter,
-                                     gi::range_blocks(), s);
-            else
-                e = gi::launch_header_init(it.d_hdr, d, it.eb, c, alpha, s);
-        }
+        pro[i] = prologue_item(it, L[i]);
         args[i] = gi::CompressArgs{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
-                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0, c.domain_x == 32, code_store_width(it.d_codes, d.nx)};
+                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0, c.domain_x == 32,
+                                   code_store_width(it.d_codes, d.nx)};
     }
+    cudaError_t e = gi::launch_prologue(pro, n, s);
     if (e == cudaSuccess) {
         timing_mark(0, 0, s);
         e = gi::launch_compress_tiles(args, n, s);  // one persistent launch for every field
         timing_mark(0, 1, s);
     }
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        const interp_compress_item &it = items[i];
-        e = gi::launch_outlier_compaction(args[i].bitmap, args[i].blockcnt, L[i].words, args[i].dims, it.d_x,
-                                          it.d_out_idx, it.d_out_val, it.out_capacity, it.d_hdr, s, false,
-                                          it.d_hist, it.cfg.radius);  // the tile kernel leaves bin R to it
+    if (e == cudaSuccess) {
+        // ordered compaction of every field in two launches; the tile kernel leaves bin R to the scan
+        gi::CompactItem ci[gi::kMaxBatch];
+        for (int i = 0; i < n; ++i) {
+            const interp_compress_item &it = items[i];
+            ci[i] = gi::CompactItem{args[i].bitmap, args[i].blockcnt, L[i].words, args[i].dims, it.d_x,
+                                    it.d_out_idx, it.d_out_val, it.out_capacity, it.d_hdr, false, it.d_hist,
+                                    it.cfg.radius};
+        }
+        e = gi::launch_outlier_compaction(ci, n, s);
     }
     return cuda_status(e);
 }
@@ -288,15 +299,18 @@ int interp_decompress_batched(const interp_decompress_item *items, int n, interp
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     gi::DecompressArgs args[gi::kMaxBatch];
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    gi::ScatterItem sc[gi::kMaxBatch];
+    int nsc = 0;
+    for (int i = 0; i < n; ++i) {
         const interp_decompress_item &it = items[i];
         const Dims d = to_dims(it.dims);
-        if (it.out_capacity > 0)
-            e = gi::launch_outlier_scatter(it.d_hdr, it.d_out_idx, it.d_out_val, it.out_capacity, it.d_xrec, s);
+        if (it.out_capacity > 0) sc[nsc++] = gi::ScatterItem{it.d_hdr, it.d_out_idx, it.d_out_val, it.out_capacity,
+                                                             it.d_xrec};
         args[i] = gi::DecompressArgs{d, it.d_anchors, it.d_codes, it.d_xrec, it.d_hdr,
                                      gi::aligned16(it.d_xrec) && d.nx % 4 == 0};
     }
+    // every field's stored outlier values in one launch, then one tile launch
+    cudaError_t e = nsc > 0 ? gi::launch_outlier_scatter(sc, nsc, s) : cudaSuccess;
     if (e == cudaSuccess) {
         timing_mark(1, 0, s);
         e = gi::launch_decompress_tiles(args, n, s);  // one persistent launch for every field
@@ -336,7 +350,10 @@ int interp_decompress_nd(int32_t ndim, const int64_t dims[3], const interp_heade
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const Dims d = to_dims(dims);
     cudaError_t e = cudaSuccess;
-    if (out_capacity > 0) e = gi::launch_outlier_scatter(d_hdr, d_out_idx, d_out_val, out_capacity, d_xrec, s);
+    if (out_capacity > 0) {
+        const gi::ScatterItem sc{d_hdr, d_out_idx, d_out_val, out_capacity, d_xrec};
+        e = gi::launch_outlier_scatter(&sc, 1, s);
+    }
     const gi::DecompressArgs args{d, d_anchors, d_codes, d_xrec, d_hdr, false};
     if (e == cudaSuccess) {
         timing_mark(1, 0, s);

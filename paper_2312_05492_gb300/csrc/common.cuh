@@ -202,6 +202,24 @@ __device__ __forceinline__ size_t tiled_word(long long gw, int words_per_row, in
 
 cudaError_t launch_header_init(interp_header *hdr, Dims d, double eb, interp_config cfg, double alpha,
                                cudaStream_t s);
+// compression set-up of n fields (1 <= n <= kMaxBatch) in two launches: zero the
+// control words, block counters and histogram of every field, then profile +
+// decision (autotune) and value range + bounds (relative) or bounds (absolute)
+struct PrologueItem {
+    const float *x;
+    Dims d;
+    double eb;
+    interp_config cfg;
+    double alpha;
+    interp_header *hdr;
+    uint32_t *counter;  // the workspace's control words (the range counter is the first)
+    int ctrl_words;
+    void *partials;
+    uint32_t *blockcnt;
+    int nblk;
+    uint32_t *hist;     // may be null
+};
+cudaError_t launch_prologue(const PrologueItem *items, int n, cudaStream_t s);
 cudaError_t launch_profile(const float *x, Dims d, interp_header *hdr, int apply_decision, cudaStream_t s,
                            int ndim = 3);
 cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, double alpha, interp_header *hdr,
@@ -214,12 +232,31 @@ size_t bitmap_words_tiled(Dims d);
 // 1-D (512-point chunks) and 2-D (16^2 chunks) variants (nd.cu); ndim 1 or 2
 cudaError_t launch_nd_compress(int ndim, const CompressArgs &a, cudaStream_t s);
 cudaError_t launch_nd_decompress(int ndim, const DecompressArgs &a, cudaStream_t s);
-cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
-                                      const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
-                                      interp_header *hdr, cudaStream_t s, bool row_major = false,
-                                      uint32_t *central_hist = nullptr, int radius = 0);  // fills bin R
-cudaError_t launch_outlier_scatter(const interp_header *hdr, const uint32_t *idx, const float *val,
-                                   uint64_t capacity, float *xrec, cudaStream_t s);
+// ordered outlier compaction of n fields (one scan launch, one write launch)
+struct CompactItem {
+    const uint32_t *bitmap;
+    uint32_t *blockcnt;
+    int64_t words;
+    Dims d;
+    const float *x;
+    uint32_t *out_idx;
+    float *out_val;
+    uint64_t capacity;
+    interp_header *hdr;
+    bool row_major;          // bitmap in row-major order (1-D / 2-D kernels), else tile-major
+    uint32_t *central_hist;  // not null: fill bin R as N minus the other bins
+    int radius;
+};
+cudaError_t launch_outlier_compaction(const CompactItem *items, int n, cudaStream_t s);
+// outlier values of n fields into their reconstructions (one launch)
+struct ScatterItem {
+    const interp_header *hdr;
+    const uint32_t *idx;
+    const float *val;
+    uint64_t capacity;
+    float *xrec;
+};
+cudaError_t launch_outlier_scatter(const ScatterItem *items, int n, cudaStream_t s);
 cudaError_t launch_histogram(const uint16_t *codes, uint64_t n, int radius, uint32_t *hist, cudaStream_t s);
 
 cudaError_t launch_quality(const uint32_t *hist, int radius, const float *x, const float *xr, uint64_t n,

@@ -8,6 +8,9 @@
 // into offsets, then one CTA per non-empty block expands its words into
 // (index, value) pairs.  Words are in ascending linear-index order, so the
 // outlier list comes out sorted by index with no sort and no atomics.
+#include <algorithm>
+#include <cstring>
+
 #include "common.cuh"
 
 namespace gi {
@@ -21,9 +24,8 @@ static_assert(WORDS_PER_THREAD * WRITE_THREADS == BITMAP_BLOCK_WORDS, "block geo
 // Exclusive scan of the block counts in place; total -> header.  With a
 // histogram whose central bin R the tile kernel left out (it is the most
 // frequent code by far), the bin is filled in here: N minus every other bin.
-__global__ void __launch_bounds__(SCAN_THREADS) k_outlier_scan(uint32_t *blockcnt, int nblk, interp_header *hdr,
-                                                              unsigned long long capacity, uint32_t *hist,
-                                                              int radius, unsigned long long n)
+__device__ void outlier_scan_block(uint32_t *blockcnt, int nblk, interp_header *hdr, unsigned long long capacity,
+                                   uint32_t *hist, int radius, unsigned long long n)
 {
     __shared__ unsigned long long warp_sum[SCAN_THREADS / 32];
     __shared__ unsigned long long carry;
@@ -79,16 +81,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_outlier_scan(uint32_t *blockcn
     }
 }
 
-__global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const uint32_t *__restrict__ bitmap,
-                                                                 const uint32_t *__restrict__ offsets,
-                                                                 long long words, int words_per_row, int nx, int ny,
-                                                                 int nz, const float *__restrict__ x,
-                                                                 uint32_t *out_idx, float *out_val,
-                                                                 unsigned long long capacity,
-                                                                 const interp_header *hdr, int nblk,
-                                                                 bool row_major)
+__device__ void outlier_write_block(const uint32_t *__restrict__ bitmap, const uint32_t *__restrict__ offsets,
+                                    long long words, int words_per_row, int nx, int ny, int nz,
+                                    const float *__restrict__ x, uint32_t *out_idx, float *out_val,
+                                    unsigned long long capacity, const interp_header *hdr, int nblk, bool row_major,
+                                    int b)
 {
-    const int b = blockIdx.x;
     const unsigned long long total = hdr->n_outliers;
     const unsigned long long start = offsets[b];
     const unsigned long long end = (b + 1 < nblk) ? offsets[b + 1] : total;
@@ -138,14 +136,68 @@ __global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const uint32_t 
     }
 }
 
-__global__ void k_outlier_scatter(const interp_header *hdr, const uint32_t *__restrict__ idx,
-                                  const float *__restrict__ val, unsigned long long capacity, float *xrec)
+// Ordered compaction of the outliers of n fields in two launches: one scan block
+// per field, then every field's non-empty bitmap blocks.
+struct CompactField {
+    const uint32_t *bitmap;
+    uint32_t *blockcnt;
+    long long words;
+    int words_per_row, nx, ny, nz;
+    const float *x;
+    uint32_t *out_idx;
+    float *out_val;
+    unsigned long long capacity;
+    interp_header *hdr;
+    int nblk;
+    bool row_major;
+    uint32_t *hist;  // fills bin R when not null
+    int radius;
+    unsigned long long n;
+    int b0;          // first write block of the field
+};
+
+struct CompactBatch {
+    CompactField f[kMaxBatch];
+    int n;
+};
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_outlier_scan(const __grid_constant__ CompactBatch B)
 {
-    unsigned long long n = hdr->n_outliers;
-    if (n > capacity) n = capacity;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        xrec[idx[i]] = val[i];
+    const CompactField &F = B.f[blockIdx.x];
+    outlier_scan_block(F.blockcnt, F.nblk, F.hdr, F.capacity, F.hist, F.radius, F.n);
+}
+
+__global__ void __launch_bounds__(WRITE_THREADS) k_outlier_write(const __grid_constant__ CompactBatch B)
+{
+    int fi = 0;
+    while (fi + 1 < B.n && B.f[fi + 1].b0 <= (int)blockIdx.x) ++fi;
+    const CompactField &F = B.f[fi];
+    outlier_write_block(F.bitmap, F.blockcnt, F.words, F.words_per_row, F.nx, F.ny, F.nz, F.x, F.out_idx,
+                        F.out_val, F.capacity, F.hdr, F.nblk, F.row_major, (int)blockIdx.x - F.b0);
+}
+
+// Outlier values of n fields into their reconstructions: `blocks` blocks per field.
+struct ScatterField {
+    const interp_header *hdr;
+    const uint32_t *idx;
+    const float *val;
+    unsigned long long capacity;
+    float *xrec;
+};
+
+struct ScatterBatch {
+    ScatterField f[kMaxBatch];
+    int n, blocks;
+};
+
+__global__ void k_outlier_scatter(const __grid_constant__ ScatterBatch B)
+{
+    const ScatterField &F = B.f[blockIdx.x / B.blocks];
+    const unsigned long long b = blockIdx.x % B.blocks;
+    unsigned long long n = F.hdr->n_outliers;
+    if (n > F.capacity) n = F.capacity;
+    for (unsigned long long i = b * blockDim.x + threadIdx.x; i < n; i += (unsigned long long)B.blocks * blockDim.x)
+        F.xrec[F.idx[i]] = F.val[i];
 }
 
 // Standalone histogram: per-CTA shared bins (register count for the central
@@ -207,29 +259,53 @@ __global__ void __launch_bounds__(HIST_THREADS) k_histogram(const uint16_t *__re
 
 }  // namespace
 
-cudaError_t launch_outlier_compaction(const uint32_t *bitmap, uint32_t *blockcnt, int64_t words, Dims d,
-                                      const float *x, uint32_t *out_idx, float *out_val, uint64_t capacity,
-                                      interp_header *hdr, cudaStream_t s, bool row_major, uint32_t *central_hist,
-                                      int radius)
+cudaError_t launch_outlier_compaction(const CompactItem *items, int n, cudaStream_t s)
 {
-    const int nblk = (int)((words + BITMAP_BLOCK_WORDS - 1) / BITMAP_BLOCK_WORDS);
-    if (nblk <= 0) return cudaSuccess;
-    const unsigned long long n = (unsigned long long)d.nz * d.ny * d.nx;
-    k_outlier_scan<<<1, SCAN_THREADS, 0, s>>>(blockcnt, nblk, hdr, (unsigned long long)capacity, central_hist,
-                                              radius, n);
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    CompactBatch B;
+    std::memset(&B, 0, sizeof(B));
+    int blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        const CompactItem &it = items[i];
+        CompactField &F = B.f[i];
+        F.bitmap = it.bitmap;
+        F.blockcnt = it.blockcnt;
+        F.words = (long long)it.words;
+        F.words_per_row = (it.d.nx + 31) / 32;
+        F.nx = it.d.nx;
+        F.ny = it.d.ny;
+        F.nz = it.d.nz;
+        F.x = it.x;
+        F.out_idx = it.out_idx;
+        F.out_val = it.out_val;
+        F.capacity = (unsigned long long)it.capacity;
+        F.hdr = it.hdr;
+        F.nblk = (int)((it.words + BITMAP_BLOCK_WORDS - 1) / BITMAP_BLOCK_WORDS);
+        F.row_major = it.row_major;
+        F.hist = it.central_hist;
+        F.radius = it.radius;
+        F.n = (unsigned long long)it.d.nz * it.d.ny * it.d.nx;
+        F.b0 = blocks;
+        blocks += F.nblk;
+    }
+    B.n = n;
+    k_outlier_scan<<<n, SCAN_THREADS, 0, s>>>(B);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int words_per_row = (d.nx + 31) / 32;
-    k_outlier_write<<<nblk, WRITE_THREADS, 0, s>>>(bitmap, blockcnt, (long long)words, words_per_row, d.nx, d.ny,
-                                                  d.nz, x, out_idx, out_val, (unsigned long long)capacity, hdr, nblk,
-                                                  row_major);
+    k_outlier_write<<<blocks, WRITE_THREADS, 0, s>>>(B);
     return cudaGetLastError();
 }
 
-cudaError_t launch_outlier_scatter(const interp_header *hdr, const uint32_t *idx, const float *val,
-                                   uint64_t capacity, float *xrec, cudaStream_t s)
+cudaError_t launch_outlier_scatter(const ScatterItem *items, int n, cudaStream_t s)
 {
-    k_outlier_scatter<<<2 * sm_count(), 256, 0, s>>>(hdr, idx, val, (unsigned long long)capacity, xrec);
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    ScatterBatch B;
+    std::memset(&B, 0, sizeof(B));
+    for (int i = 0; i < n; ++i) B.f[i] = ScatterField{items[i].hdr, items[i].idx, items[i].val,
+                                                      (unsigned long long)items[i].capacity, items[i].xrec};
+    B.n = n;
+    B.blocks = std::max(1, 2 * sm_count() / n);
+    k_outlier_scatter<<<B.blocks * n, 256, 0, s>>>(B);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,9 @@
 //     device header by the last CTA of the range reduction;
 //   - the 4x4x4 sampling profile (two cubic splines per axis, Sec. IV-B.1)
 //     and the configuration decision (Sec. IV-B.2), in one small CTA.
+#include <algorithm>
 #include <cfloat>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -77,18 +79,18 @@ __device__ __forceinline__ void range_acc(float v, float &lo, float &hi, unsigne
     }
 }
 
-// Grid-stride min/max over finite values with 4 independent 16-byte loads in
-// flight per thread; the last CTA to finish reduces the per-CTA partials and
-// writes the header (no second launch, no host round trip).
-__global__ void __launch_bounds__(RANGE_THREADS) k_range(const float *__restrict__ x, unsigned long long n, int vec,
-                                                        RangePartial *partials, unsigned int *counter,
-                                                        interp_header *hdr, Dims d, double eb, interp_config cfg,
-                                                        double alpha, float *out_range)
+// Block b of the nb blocks that reduce one field: grid-stride min/max over
+// finite values with 4 independent 16-byte loads in flight per thread; the last
+// block to finish reduces the per-block partials and writes the header (no
+// second launch, no host round trip).  RANGE_THREADS threads per block.
+__device__ void range_block(const float *__restrict__ x, unsigned long long n, int vec, RangePartial *partials,
+                            unsigned int *counter, interp_header *hdr, Dims d, double eb, const interp_config &cfg,
+                            double alpha, float *out_range, int b, int nb)
 {
     float lo = INFINITY, hi = -INFINITY;
     unsigned long long bad = 0;
-    const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long tid = (unsigned long long)b * RANGE_THREADS + threadIdx.x;
+    const unsigned long long nthreads = (unsigned long long)nb * RANGE_THREADS;
     unsigned long long done = 0;
     if (vec) {
         const float4 *x4 = reinterpret_cast<const float4 *>(x);
@@ -135,9 +137,9 @@ __global__ void __launch_bounds__(RANGE_THREADS) k_range(const float *__restrict
             p.hi = fmaxf(p.hi, warp_part[w].hi);
             p.nonfinite += warp_part[w].nonfinite;
         }
-        partials[blockIdx.x] = p;
+        partials[b] = p;
         __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        last = atomicAdd(counter, 1u) == (unsigned int)nb - 1;
     }
     __syncthreads();
     if (!last) return;
@@ -145,8 +147,8 @@ __global__ void __launch_bounds__(RANGE_THREADS) k_range(const float *__restrict
     lo = INFINITY;
     hi = -INFINITY;
     bad = 0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += RANGE_THREADS) {
-        const RangePartial p = partials[b];
+    for (int k = threadIdx.x; k < nb; k += RANGE_THREADS) {
+        const RangePartial p = partials[k];
         lo = fminf(lo, p.lo);
         hi = fmaxf(hi, p.hi);
         bad += p.nonfinite;
@@ -181,6 +183,14 @@ __global__ void __launch_bounds__(RANGE_THREADS) k_range(const float *__restrict
     }
 }
 
+__global__ void __launch_bounds__(RANGE_THREADS) k_range(const float *__restrict__ x, unsigned long long n, int vec,
+                                                        RangePartial *partials, unsigned int *counter,
+                                                        interp_header *hdr, Dims d, double eb, interp_config cfg,
+                                                        double alpha, float *out_range)
+{
+    range_block(x, n, vec, partials, counter, hdr, d, eb, cfg, alpha, out_range, blockIdx.x, gridDim.x);
+}
+
 // ----------------------------------------------------- sampling profile
 // Sample coordinate j (0..3) along an axis of length n: a uniform 4-point
 // grid kept 12 points (or half the axis) away from both ends.
@@ -196,13 +206,15 @@ constexpr int PROFILE_SAMPLES = 64;
 //   |x - NAK cubic|, |x - natural cubic|, |x - linear|,
 //   2 |x - linear (stride 2)|, |x - quad-left (stride 2)| + |x - quad-right (stride 2)|.
 // Sums per (axis, term) in sample order (z, y, x ascending), in double.
-__global__ void __launch_bounds__(3 * PROFILE_SAMPLES) k_profile(const float *__restrict__ x, Dims d,
-                                                                interp_header *hdr, int apply, int first_axis)
+// The first 3 * PROFILE_SAMPLES threads of the block compute; every thread of
+// the block takes part in its barriers.
+__device__ void profile_block(const float *__restrict__ x, Dims d, interp_header *hdr, int apply, int first_axis)
 {
     __shared__ double terms[3][5][PROFILE_SAMPLES];
     __shared__ double prof[18];
     const int t = threadIdx.x;
-    const int axis = t / PROFILE_SAMPLES, smp = t % PROFILE_SAMPLES;
+    const bool worker = t < 3 * PROFILE_SAMPLES;
+    const int axis = worker ? t / PROFILE_SAMPLES : 0, smp = t % PROFILE_SAMPLES;
     const int n3[3] = {d.nz, d.ny, d.nx};
     const long long st[3] = {(long long)d.ny * d.nx, (long long)d.nx, 1};
     const int c[3] = {sample_coord(d.nz, smp / 16), sample_coord(d.ny, (smp / 4) % 4), sample_coord(d.nx, smp % 4)};
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(3 * PROFILE_SAMPLES) k_profile(const float *__
     const long long sd = st[axis];
     const double xv = (double)x[i];
     double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0;
-    const bool chunked = axis >= first_axis;  // the leading axes of 1-D / 2-D data are not profiled
+    const bool chunked = worker && axis >= first_axis;  // the leading axes of 1-D / 2-D data are not profiled
     if (chunked && n - 3 >= 0 && n + 3 <= nd - 1) {
         const float m3 = x[i - 3 * sd], m1 = x[i - sd], p1 = x[i + sd], p3 = x[i + 3 * sd];
         t0 = fabs(xv - (double)sp_cubic(cubic_coeffs(0), m3, m1, p1, p3));
@@ -223,11 +235,13 @@ __global__ void __launch_bounds__(3 * PROFILE_SAMPLES) k_profile(const float *__
         t3 = 2.0 * fabs(xv - (double)sp_linear(m1, p1));
         t4 = fabs(xv - (double)sp_quad_left(m3, m1, p1)) + fabs(xv - (double)sp_quad_right(m1, p1, p3));
     }
-    terms[axis][0][smp] = t0;
-    terms[axis][1][smp] = t1;
-    terms[axis][2][smp] = t2;
-    terms[axis][3][smp] = t3;
-    terms[axis][4][smp] = t4;
+    if (worker) {
+        terms[axis][0][smp] = t0;
+        terms[axis][1][smp] = t1;
+        terms[axis][2][smp] = t2;
+        terms[axis][3][smp] = t3;
+        terms[axis][4][smp] = t4;
+    }
     __syncthreads();
     if (t < 15) {
         const int a = t % 3, term = t / 3;
@@ -275,6 +289,83 @@ __global__ void __launch_bounds__(3 * PROFILE_SAMPLES) k_profile(const float *__
     hdr->cfg.level_kind[2] = 1;
 }
 
+__global__ void __launch_bounds__(3 * PROFILE_SAMPLES) k_profile(const float *__restrict__ x, Dims d,
+                                                                interp_header *hdr, int apply, int first_axis)
+{
+    profile_block(x, d, hdr, apply, first_axis);
+}
+
+// The set-up of compression for every field of a call in one launch: per field,
+// a block for the sampling profile and decision (when autotuning), then the
+// blocks of its value range and bounds (relative mode) or one block writing the
+// bounds (absolute mode).  The profile writes only the header's profile and
+// decided configuration, the bounds only the other fields, so they may run
+// concurrently.
+struct PrologueField {
+    const float *x;
+    unsigned long long n;
+    int vec;
+    RangePartial *partials;
+    unsigned int *counter;
+    interp_header *hdr;
+    Dims d;
+    double eb;
+    interp_config cfg;
+    double alpha;
+    int first_axis;
+    int b0;        // first block of the field
+    int nprof;     // 1 when autotuning, else 0
+    int nrange;    // range blocks (relative mode), or 1 (absolute mode)
+};
+
+struct PrologueBatch {
+    PrologueField f[kMaxBatch];
+    int n;
+};
+
+__global__ void __launch_bounds__(RANGE_THREADS) k_prologue(const __grid_constant__ PrologueBatch B)
+{
+    const int b = blockIdx.x;
+    int fi = 0;
+    while (fi + 1 < B.n && B.f[fi + 1].b0 <= b) ++fi;
+    const PrologueField &F = B.f[fi];
+    const int lb = b - F.b0;
+    if (lb < F.nprof) {
+        profile_block(F.x, F.d, F.hdr, 1, F.first_axis);
+        return;
+    }
+    if (F.cfg.eb_mode)
+        range_block(F.x, F.n, F.vec, F.partials, F.counter, F.hdr, F.d, F.eb, F.cfg, F.alpha, nullptr,
+                    lb - F.nprof, F.nrange);
+    else if (threadIdx.x == 0)
+        write_bounds(F.hdr, F.d, F.eb, F.cfg, F.alpha, 0.0f, 0.0f, 0ull);
+}
+
+// Zero the parts of every field's workspace that must start at zero (control
+// words, outlier block counters) and its histogram, one block per field.
+struct ZeroField {
+    uint32_t *ctrl;
+    int ctrl_words;
+    uint32_t *blockcnt;
+    int nblk;
+    uint32_t *hist;
+    int bins;
+};
+
+struct ZeroBatch {
+    ZeroField f[kMaxBatch];
+    int n;
+};
+
+__global__ void __launch_bounds__(512) k_zero(const __grid_constant__ ZeroBatch B)
+{
+    const ZeroField &F = B.f[blockIdx.x];
+    for (int i = threadIdx.x; i < F.ctrl_words; i += 512) F.ctrl[i] = 0u;
+    for (int i = threadIdx.x; i < F.nblk; i += 512) F.blockcnt[i] = 0u;
+    if (F.hist)
+        for (int i = threadIdx.x; i < F.bins; i += 512) F.hist[i] = 0u;
+}
+
 }  // namespace
 
 int sm_count()
@@ -308,6 +399,51 @@ cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, d
     if (nblocks > RANGE_MAX_BLOCKS) nblocks = RANGE_MAX_BLOCKS;
     k_range<<<nblocks, RANGE_THREADS, 0, s>>>(x, n, vec, reinterpret_cast<RangePartial *>(partials), counter, hdr, d,
                                              eb, cfg, alpha, out_range);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prologue(const PrologueItem *items, int n, cudaStream_t s)
+{
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    PrologueBatch B;
+    std::memset(&B, 0, sizeof(B));
+    ZeroBatch Z;
+    std::memset(&Z, 0, sizeof(Z));
+    int blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        const PrologueItem &it = items[i];
+        PrologueField &F = B.f[i];
+        F.x = it.x;
+        F.d = it.d;
+        F.n = (unsigned long long)it.d.nz * it.d.ny * it.d.nx;
+        F.vec = (reinterpret_cast<uintptr_t>(it.x) % 16) == 0;
+        F.partials = reinterpret_cast<RangePartial *>(it.partials);
+        F.counter = it.counter;
+        F.hdr = it.hdr;
+        F.eb = it.eb;
+        F.cfg = it.cfg;
+        F.alpha = it.alpha;
+        F.first_axis = (it.cfg.ndim == 1 || it.cfg.ndim == 2) ? 3 - it.cfg.ndim : 0;
+        F.b0 = blocks;
+        F.nprof = it.cfg.autotune ? 1 : 0;
+        // range blocks: about 32 K values each, at most range_blocks()
+        const unsigned long long want = (F.n + 32767) / 32768;
+        F.nrange = it.cfg.eb_mode ? (int)std::max(1ull, std::min<unsigned long long>(want, range_blocks())) : 1;
+        blocks += F.nprof + F.nrange;
+        ZeroField &zf = Z.f[i];
+        zf.ctrl = it.counter;
+        zf.ctrl_words = it.ctrl_words;
+        zf.blockcnt = it.blockcnt;
+        zf.nblk = it.nblk;
+        zf.hist = it.hist;
+        zf.bins = 2 * it.cfg.radius;
+    }
+    B.n = n;
+    Z.n = n;
+    k_zero<<<n, 512, 0, s>>>(Z);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_prologue<<<blocks, RANGE_THREADS, 0, s>>>(B);
     return cudaGetLastError();
 }
 

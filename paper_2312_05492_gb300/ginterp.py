@@ -30,10 +30,11 @@ FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress",
              "interp_huffman_chunks", "interp_huffman_capacity_words", "interp_huffman_workspace_bytes",
              "interp_huffman_encode", "interp_huffman_decode", "interp_anchor_count_nd", "interp_decompress_nd")
 
-# kernels each call launches (memsets excluded): compress = [profile] + range or
-# header + tiles + outlier scan + outlier write; decompress = scatter + tiles
+# kernels each call launches, for one field or a whole batch: compress = zeroing +
+# set-up (profile, range, bounds) + tiles + outlier scan + outlier write;
+# decompress = outlier scatter + tiles
 def launches_compress(cfg: "Config") -> int:
-    return (1 if cfg.autotune else 0) + 1 + 1 + 2
+    return 5
 
 
 LAUNCHES_DECOMPRESS = 2

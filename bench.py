@@ -753,14 +753,14 @@ def run_batch(args, rank, world, local):
         return a.elapsed_time(b) / k
 
     k = max(10, min(args.steps, 100))
-    ms_single, ms_batch, ms_graph, exact, bound = compare_batch(G, xs, ebs, cfgs, caps, k, timed, stream)
+    ms_single, ms_batch, ms_graph, exact, bound, sched = compare_batch(G, xs, ebs, cfgs, caps, k, timed, stream)
     gbs = lambda ms, nb=nbytes: round(nb / (ms * 1e-3) / 1e9, 2)  # noqa: E731
     # many smaller uneven fields (each fills a fraction of the GPU): where batching pays
     sx, sebs, scfgs = small_batch_fields(dev)
     torch.cuda.empty_cache()
     # full outlier capacity: the rough k^-2 fields at rel 1e-4 can exceed N/16 outliers
-    s_single, s_batch, s_graph, s_exact, s_bound = compare_batch(G, sx, sebs, scfgs, [x.numel() for x in sx],
-                                                               k, timed, stream)
+    s_single, s_batch, s_graph, s_exact, s_bound, s_sched = compare_batch(G, sx, sebs, scfgs,
+                                                                         [x.numel() for x in sx], k, timed, stream)
     s_bytes = sum(4 * x.numel() for x in sx)
     return {"metric": "batched compress+decompress GB/s, 3 uneven fields per step",
             "value": gbs(ms_graph), "unit": "GB/s", "n_gpus": 1, "steps": k, "warmup": max(args.warmup, 3),
@@ -771,12 +771,15 @@ def run_batch(args, rank, world, local):
             "one_call_per_field_gbs": gbs(ms_single), "batched_eager_gbs": gbs(ms_batch),
             "batched_graph_gbs": gbs(ms_graph), "speedup_vs_single": round(ms_single / ms_graph, 3),
             "bit_exact_vs_single": bool(exact), "bound_ok": bool(bound),
+            "tile_schedule": {**sched, "what": "[slabs per work item, CTAs per SM] (0 = automatic) picked by "
+                                              "the library's autotuner (interp_tune_batched)"},
             "small_fields": {"workload": f"{len(sx)} uneven GRF fields, edges 100..180, beta 2..4, rel eb 1e-2..1e-4",
                              "input_mb": round(s_bytes / 1e6, 1),
                              "l2_flush": "not needed" if s_bytes > 129e6 else "NEEDED: inputs fit the L2",
                              "one_call_per_field_gbs": gbs(s_single, s_bytes),
                              "batched_eager_gbs": gbs(s_batch, s_bytes), "batched_graph_gbs": gbs(s_graph, s_bytes),
                              "speedup_vs_single": round(s_single / s_graph, 3), "bit_exact_vs_single": bool(s_exact),
+                             "tile_schedule": s_sched,
                              "bound_ok": bool(s_bound)},
             "gpu_launches": (G.launches_compress(cfgs[0]) + G.LAUNCHES_DECOMPRESS) * k}
 
@@ -811,6 +814,7 @@ def compare_batch(G, xs, ebs, cfgs, caps, k, timed, stream):
 
     batch = G.Batch(xs, ebs, cfgs, capacities=caps)
     ms_single = timed(step_single, k)
+    batch.tune(stream)  # the library's tile-schedule autotuner (cached by the batch's shapes)
     ms_batch = timed(batch.round_trip, k)
     side = torch.cuda.Stream()
     side.wait_stream(stream)
@@ -829,8 +833,10 @@ def compare_batch(G, xs, ebs, cfgs, caps, k, timed, stream):
                 for a, b, oa, ob in zip(batch.fields, singles.fields, batch.outs, singles.outs))
     bound = all(float((o - x).abs().max()) <= level0_bound(f.host_header(refresh=True))
                 for o, x, f in zip(batch.outs, xs, batch.fields))
+    sched = {"compress": [batch.csched.run, batch.csched.ctas_per_sm],
+             "decompress": [batch.dsched.run, batch.dsched.ctas_per_sm]}
     del graph, batch, singles
-    return ms_single, ms_batch, ms_graph, exact, bound
+    return ms_single, ms_batch, ms_graph, exact, bound, sched
 
 
 def main():

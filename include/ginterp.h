@@ -196,6 +196,37 @@ typedef struct {
 int interp_compress_batched(const interp_compress_item *h_items, int n, interp_stream_t stream);
 int interp_decompress_batched(const interp_decompress_item *h_items, int n, interp_stream_t stream);
 
+/* Schedule of the persistent tile launch of a (batched) call.  The paper has no
+ * counterpart: it is a launch parameter of this library's GPU mapping.  run = slabs of 8
+ * planes per work item (0 = the library's cost model; larger runs recompute fewer
+ * closing planes, shorter ones balance the CTAs better), ctas_per_sm = resident CTAs
+ * per SM (0 = the occupancy limit; a smaller value caps it).  Outputs do not depend on
+ * the schedule, bit for bit. */
+typedef struct {
+    int32_t run;
+    int32_t ctas_per_sm;
+} interp_tile_schedule;
+
+/* interp_compress_batched / interp_decompress_batched with an explicit schedule
+ * (h_sched may be NULL: automatic).  Negative fields are INTERP_EINVAL. */
+int interp_compress_batched_scheduled(const interp_compress_item *h_items, int n, const interp_tile_schedule *h_sched,
+                                      interp_stream_t stream);
+int interp_decompress_batched_scheduled(const interp_decompress_item *h_items, int n,
+                                        const interp_tile_schedule *h_sched, interp_stream_t stream);
+
+/* Tile-schedule autotuner of a batch: runs the batch's compression (h_citems) and then
+ * its decompression (h_ditems, which must read what h_citems write) with every
+ * candidate schedule (runs 1, 2, 4, 8, 16, whole columns and the cost model's choice;
+ * the occupancy limit and one or two CTAs per SM fewer), times each on `stream` with
+ * CUDA events (one warm-up call, then the mean of two) and returns the fastest in
+ * h_csched / h_dsched.  The outputs are written and valid afterwards.  Synchronises
+ * `stream`.  Results are cached by the fields' shapes, configurations, bounds and
+ * buffer alignment: a later call with the same batch returns the cached schedules
+ * without running anything unless force != 0. */
+int interp_tune_batched(const interp_compress_item *h_citems, const interp_decompress_item *h_ditems, int n,
+                        int32_t force, interp_tile_schedule *h_csched, interp_tile_schedule *h_dsched,
+                        interp_stream_t stream);
+
 /* Histogram of quant-codes (Fig. 1 "histogram", Sec. V-A): d_hist[c] = #{i : codes[i] = c}
  * for c in [0, 2R); d_hist (2R uint32) is zeroed by the callee.  Codes >= 2R are ignored. */
 int qcode_histogram(const uint16_t *d_codes, uint64_t n, int32_t radius, uint32_t *d_hist,

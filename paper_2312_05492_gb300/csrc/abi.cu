@@ -216,6 +216,13 @@ int compress_nd(const interp_compress_item &it, interp_stream_t stream)
 
 int interp_compress_batched(const interp_compress_item *items, int n, interp_stream_t stream)
 {
+    return interp_compress_batched_scheduled(items, n, nullptr, stream);
+}
+
+int interp_compress_batched_scheduled(const interp_compress_item *items, int n, const interp_tile_schedule *sched,
+                                      interp_stream_t stream)
+{
+    if (sched && (sched->run < 0 || sched->ctas_per_sm < 0)) return INTERP_EINVAL;
     if (!items || n < 1 || n > gi::kMaxBatch) return INTERP_EINVAL;
     WsLayout L[gi::kMaxBatch];
     for (int i = 0; i < n; ++i) {  // every argument is checked before anything is enqueued
@@ -247,7 +254,8 @@ int interp_compress_batched(const interp_compress_item *items, int n, interp_str
     cudaError_t e = gi::launch_prologue(pro, n, s);
     if (e == cudaSuccess) {
         timing_mark(0, 0, s);
-        e = gi::launch_compress_tiles(args, n, s);  // one persistent launch for every field
+        const gi::TileSchedule ts{sched ? sched->run : 0, sched ? sched->ctas_per_sm : 0};
+        e = gi::launch_compress_tiles(args, n, s, &ts);  // one persistent launch for every field
         timing_mark(0, 1, s);
     }
     if (e == cudaSuccess) {
@@ -290,6 +298,13 @@ int interp_compress(const float *d_x, const int64_t dims[3], double eb, const in
 
 int interp_decompress_batched(const interp_decompress_item *items, int n, interp_stream_t stream)
 {
+    return interp_decompress_batched_scheduled(items, n, nullptr, stream);
+}
+
+int interp_decompress_batched_scheduled(const interp_decompress_item *items, int n,
+                                        const interp_tile_schedule *sched, interp_stream_t stream)
+{
+    if (sched && (sched->run < 0 || sched->ctas_per_sm < 0)) return INTERP_EINVAL;
     if (!items || n < 1 || n > gi::kMaxBatch) return INTERP_EINVAL;
     for (int i = 0; i < n; ++i) {
         const interp_decompress_item &it = items[i];
@@ -313,7 +328,8 @@ int interp_decompress_batched(const interp_decompress_item *items, int n, interp
     cudaError_t e = nsc > 0 ? gi::launch_outlier_scatter(sc, nsc, s) : cudaSuccess;
     if (e == cudaSuccess) {
         timing_mark(1, 0, s);
-        e = gi::launch_decompress_tiles(args, n, s);  // one persistent launch for every field
+        const gi::TileSchedule ts{sched ? sched->run : 0, sched ? sched->ctas_per_sm : 0};
+        e = gi::launch_decompress_tiles(args, n, s, &ts);  // one persistent launch for every field
         timing_mark(1, 1, s);
     }
     return cuda_status(e);

@@ -226,8 +226,15 @@ cudaError_t launch_range(const float *x, Dims d, double eb, interp_config cfg, d
                          void *partials, unsigned int *counter, int nblocks, cudaStream_t s,
                          float *out_range = nullptr);  // hdr == nullptr: write {vmin, vmax} to out_range
 // one persistent launch over the tiles of n fields (1 <= n <= kMaxBatch)
-cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s);
-cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s);
+// schedule of a persistent tile launch: slabs per work item and CTAs per SM (0 = automatic)
+struct TileSchedule {
+    int run;
+    int ctas_per_sm;
+};
+cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s,
+                                  const TileSchedule *sched = nullptr);
+cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s,
+                                    const TileSchedule *sched = nullptr);
 size_t bitmap_words_tiled(Dims d);
 // 1-D (512-point chunks) and 2-D (16^2 chunks) variants (nd.cu); ndim 1 or 2
 cudaError_t launch_nd_compress(int ndim, const CompressArgs &a, cudaStream_t s);

@@ -23,6 +23,7 @@
 // s) give all 1, 2 or 4 predictions of the segment from registers.
 // Full-chunk stencils are fixed (Fig. 3); chunks truncated by the field's far
 // edge take the neighbour-count rule point by point.
+#include <algorithm>
 #include <cstring>
 
 #include "tma.cuh"
@@ -1317,8 +1318,8 @@ Field field_of(Dims d)
 
 // Split the slabs of every column of every field into runs of one common
 // length so that the busiest CTA of the persistent grid has the least work
-// (each run start recomputes one plane).
-void plan_runs(Field *fs, int n, int grid)
+// (each run start recomputes one plane); `forced` > 0 imposes the length.
+void plan_runs(Field *fs, int n, int grid, int forced = 0)
 {
     int max_slabs = 1;
     for (int i = 0; i < n; ++i) max_slabs = max(max_slabs, fs[i].slabs);
@@ -1339,6 +1340,7 @@ void plan_runs(Field *fs, int n, int grid)
             best_run = run;
         }
     }
+    if (forced > 0) best_run = forced;
     for (int i = 0; i < n; ++i) {
         fs[i].run = min(best_run, fs[i].slabs);
         fs[i].items = fs[i].cols * ((fs[i].slabs + fs[i].run - 1) / fs[i].run);
@@ -1353,18 +1355,27 @@ size_t bitmap_words_tiled(Dims d)
     return cols * (size_t)d.nz * OY;
 }
 
-cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s)
+// The grid of a persistent launch: the occupancy limit, or fewer CTAs per SM
+// when the schedule asks for them.
+int scheduled_grid(int grid, const TileSchedule *sched)
+{
+    if (sched && sched->ctas_per_sm > 0) grid = std::min(grid, sched->ctas_per_sm * sm_count());
+    return std::max(grid, 1);
+}
+
+cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t s, const TileSchedule *sched)
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     int grid = 0;
     auto kernel = n > 1 ? k_compress<true> : k_compress<false>;
     cudaError_t e = prepare(kernel, kCompressSmem, compress_grid[n > 1 ? 1 : 0], grid);
     if (e != cudaSuccess) return e;
+    grid = scheduled_grid(grid, sched);
     thread_local CBatch B;  // large parameter block, filled on the host
     std::memset(&B, 0, sizeof(B));
     Field fs[kMaxBatch];
     for (int i = 0; i < n; ++i) fs[i] = field_of(args[i].dims);
-    plan_runs(fs, n, grid);
+    plan_runs(fs, n, grid, sched ? sched->run : 0);
     int items = 0;
     for (int i = 0; i < n; ++i) {
         B.fld[i].a = args[i];
@@ -1382,18 +1393,19 @@ cudaError_t launch_compress_tiles(const CompressArgs *args, int n, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s)
+cudaError_t launch_decompress_tiles(const DecompressArgs *args, int n, cudaStream_t s, const TileSchedule *sched)
 {
     if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
     int grid = 0;
     cudaError_t e = n > 1 ? prepare(k_decompress<true>, kDecompressSmem, decompress_grid_multi, grid)
                           : prepare(k_decompress<false>, kDecompressSmem, decompress_grid, grid);
     if (e != cudaSuccess) return e;
+    grid = scheduled_grid(grid, sched);
     thread_local DBatch B;
     std::memset(&B, 0, sizeof(B));
     Field fs[kMaxBatch];
     for (int i = 0; i < n; ++i) fs[i] = field_of(args[i].dims);
-    plan_runs(fs, n, grid);
+    plan_runs(fs, n, grid, sched ? sched->run : 0);
     int items = 0;
     for (int i = 0; i < n; ++i) {
         B.fld[i].a = args[i];

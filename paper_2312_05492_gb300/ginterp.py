@@ -28,7 +28,8 @@ FUNCTIONS = ("interp_anchor_count", "interp_workspace_bytes", "interp_compress",
              "interp_decompress_batched", "interp_status_string", "interp_alpha", "interp_value_range",
              "interp_quality_workspace_bytes", "interp_quality_report", "interp_huffman_codebook",
              "interp_huffman_chunks", "interp_huffman_capacity_words", "interp_huffman_workspace_bytes",
-             "interp_huffman_encode", "interp_huffman_decode", "interp_anchor_count_nd", "interp_decompress_nd")
+             "interp_huffman_encode", "interp_huffman_decode", "interp_anchor_count_nd", "interp_decompress_nd",
+             "interp_compress_batched_scheduled", "interp_decompress_batched_scheduled", "interp_tune_batched")
 
 # kernels each call launches, for one field or a whole batch: compress = zeroing +
 # set-up (profile, range, bounds) + tiles + outlier scan + outlier write;
@@ -68,6 +69,10 @@ class interp_compress_item(ctypes.Structure):
                 ("d_out_idx", ctypes.c_void_p), ("d_out_val", ctypes.c_void_p), ("out_capacity", ctypes.c_uint64),
                 ("d_hist", ctypes.c_void_p), ("d_hdr", ctypes.c_void_p), ("d_ws", ctypes.c_void_p),
                 ("ws_bytes", ctypes.c_size_t)]
+
+
+class interp_tile_schedule(ctypes.Structure):
+    _fields_ = [("run", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class interp_decompress_item(ctypes.Structure):
@@ -144,6 +149,15 @@ def load() -> ctypes.CDLL:
     lib.interp_compress_batched.argtypes = [ctypes.POINTER(interp_compress_item), ctypes.c_int, P]
     lib.interp_decompress_batched.restype = ctypes.c_int
     lib.interp_decompress_batched.argtypes = [ctypes.POINTER(interp_decompress_item), ctypes.c_int, P]
+    sched_p = ctypes.POINTER(interp_tile_schedule)
+    lib.interp_compress_batched_scheduled.restype = ctypes.c_int
+    lib.interp_compress_batched_scheduled.argtypes = [ctypes.POINTER(interp_compress_item), ctypes.c_int, sched_p, P]
+    lib.interp_decompress_batched_scheduled.restype = ctypes.c_int
+    lib.interp_decompress_batched_scheduled.argtypes = [ctypes.POINTER(interp_decompress_item), ctypes.c_int,
+                                                        sched_p, P]
+    lib.interp_tune_batched.restype = ctypes.c_int
+    lib.interp_tune_batched.argtypes = [ctypes.POINTER(interp_compress_item), ctypes.POINTER(interp_decompress_item),
+                                        ctypes.c_int, i32, sched_p, sched_p, P]
     lib.interp_status_string.restype = ctypes.c_char_p
     lib.interp_status_string.argtypes = [ctypes.c_int]
     _lib = lib
@@ -253,6 +267,26 @@ def interp_compress_batched(items, stream) -> int:
 def interp_decompress_batched(items, stream) -> int:
     arr = (interp_decompress_item * len(items))(*items)
     return load().interp_decompress_batched(arr, len(items), stream)
+
+
+def interp_compress_batched_scheduled(items, sched, stream) -> int:
+    arr = (interp_compress_item * len(items))(*items)
+    return load().interp_compress_batched_scheduled(arr, len(items), ctypes.byref(sched) if sched else None, stream)
+
+
+def interp_decompress_batched_scheduled(items, sched, stream) -> int:
+    arr = (interp_decompress_item * len(items))(*items)
+    return load().interp_decompress_batched_scheduled(arr, len(items), ctypes.byref(sched) if sched else None, stream)
+
+
+def interp_tune_batched(citems, ditems, stream, force: bool = False):
+    """(compression schedule, decompression schedule) the library's autotuner picks."""
+    ca = (interp_compress_item * len(citems))(*citems)
+    da = (interp_decompress_item * len(ditems))(*ditems)
+    cs, ds = interp_tile_schedule(), interp_tile_schedule()
+    _check(load().interp_tune_batched(ca, da, len(citems), int(force), ctypes.byref(cs), ctypes.byref(ds), stream),
+           "interp_tune_batched")
+    return cs, ds
 
 
 def interp_status_string(rc: int) -> str:
@@ -621,12 +655,21 @@ class Batch:
         self._citems = [compress_item(x, e, c, b, w) for x, e, c, b, w in
                         zip(self.xs, self.ebs, self.cfgs, self.bufs, self.ws)]
         self._ditems = [decompress_item(cf, o) for cf, o in zip(self.fields, self.outs)]
+        self.csched = self.dsched = None  # tile schedules (None: the library's cost model)
+
+    def tune(self, stream=None, force: bool = False):
+        """Let the library's autotuner pick the tile schedules of this batch (times the
+        candidates on the device; cached by the batch's shapes).  Synchronises."""
+        self.csched, self.dsched = interp_tune_batched(self._citems, self._ditems, _stream_ptr(stream), force)
+        return self.csched, self.dsched
 
     def compress(self, stream=None):
-        _check(interp_compress_batched(self._citems, _stream_ptr(stream)), "interp_compress_batched")
+        _check(interp_compress_batched_scheduled(self._citems, self.csched, _stream_ptr(stream)),
+               "interp_compress_batched")
 
     def decompress(self, stream=None):
-        _check(interp_decompress_batched(self._ditems, _stream_ptr(stream)), "interp_decompress_batched")
+        _check(interp_decompress_batched_scheduled(self._ditems, self.dsched, _stream_ptr(stream)),
+               "interp_decompress_batched")
 
     def round_trip(self, stream=None):
         self.compress(stream)

@@ -93,3 +93,56 @@ def test_batched_cuda_graph_replay():
     for (codes, out), f, o in zip(ref, b.fields, b.outs):
         assert torch.equal(codes, f.codes)
         assert torch.equal(out.view(torch.int32), o.view(torch.int32))
+
+
+def test_batched_matches_the_oracle_directly():
+    """Every field of a batch against the oracle run on that field alone (codes,
+    anchors, outliers, histogram, reconstruction, bit for bit): no shared mistake of
+    the batched and the single-field path can pass."""
+    import oracle as O
+    from _parity import bits
+    xs, ebs, cfgs = _batch_inputs()
+    b = G.Batch(xs, ebs, cfgs, capacities=[x.numel() for x in xs])
+    b.round_trip()
+    torch.cuda.synchronize()
+    for x, eb, cfg, cf, xr in zip(xs, ebs, cfgs, b.fields, b.outs):
+        xn = x.cpu().numpy()
+        h = cf.host_header(refresh=True)
+        eb_abs, e, twoe, inv2e = O.bounds_for(xn, eb, cfg.eb_mode)
+        ocfg = O.autotune(xn, cfg.radius) if cfg.autotune else O.Config(
+            order=tuple(cfg.dim_order), level_kind=tuple(cfg.level_kind), cubic_kind=tuple(cfg.cubic_kind),
+            radius=cfg.radius)
+        assert tuple(h.cfg.dim_order) == tuple(ocfg.order) and tuple(h.cfg.level_kind) == tuple(ocfg.level_kind)
+        oc = O.compress(xn, ocfg, e, twoe, inv2e, eb_abs)
+        assert np.array_equal(cf.codes.cpu().numpy().view(np.uint16).reshape(xn.shape), oc.codes)
+        assert np.array_equal(bits(cf.anchors.cpu().numpy()), bits(oc.anchors))
+        k = int(h.n_outliers)
+        assert k == oc.n_outliers
+        assert np.array_equal(cf.out_idx[:k].cpu().numpy().view(np.uint32), oc.out_idx[:k])
+        assert np.array_equal(bits(cf.out_val[:k].cpu().numpy()), bits(oc.out_val[:k]))
+        assert np.array_equal(cf.hist.cpu().numpy().view(np.uint32), O.histogram(oc.codes, cfg.radius))
+        assert np.array_equal(bits(xr.cpu().numpy()), bits(oc.xrec))
+
+
+def test_tuned_schedules_change_nothing_but_time():
+    """The tile-schedule autotuner picks a schedule per direction from its candidates
+    (cached by the batch's shapes); every candidate, the picked ones included, gives
+    the results of the default schedule bit for bit."""
+    xs, ebs, cfgs = _batch_inputs()
+    ref = G.Batch(xs, ebs, cfgs, capacities=[x.numel() for x in xs])
+    ref.round_trip()
+    b = G.Batch(xs, ebs, cfgs, capacities=[x.numel() for x in xs])
+    cs, ds = b.tune()
+    assert cs.run >= 0 and ds.run >= 0 and cs.ctas_per_sm in (0, 3, 4) and ds.ctas_per_sm in (0, 3, 4)
+    again = b.tune()  # cached: the same picks
+    assert (again[0].run, again[0].ctas_per_sm, again[1].run, again[1].ctas_per_sm) == \
+        (cs.run, cs.ctas_per_sm, ds.run, ds.ctas_per_sm)
+    for sched in (G.interp_tile_schedule(1, 3), G.interp_tile_schedule(3, 0), cs):
+        b.csched, b.dsched = sched, sched
+        for o in b.outs:
+            o.zero_()
+        b.round_trip()
+        torch.cuda.synchronize()
+        for i in range(len(xs)):
+            _same(ref.fields[i], ref.outs[i], b.fields[i], b.outs[i])
+    assert G.interp_compress_batched_scheduled(b._citems, G.interp_tile_schedule(-1, 0), None) == G.INTERP_EINVAL

@@ -55,8 +55,11 @@ typedef enum {
 /* device-side status bits (interp_header.status) */
 #define INTERP_STATUS_CAPACITY 1u  /* more outliers than out_capacity; n_outliers is the true count */
 #define INTERP_STATUS_NONFINITE 2u /* the field holds NaN/Inf (stored losslessly as outliers) */
-#define INTERP_STATUS_TIMEOUT 4u   /* a tile kernel gave up waiting for an input transfer (its
-                                      output is incomplete); set by compression and decompression */
+#define INTERP_STATUS_TIMEOUT 4u   /* a tile kernel gave up waiting for an input transfer;
+                                      set by compression and decompression.  The call's outputs
+                                      are then invalid, and a transfer that never completed
+                                      points to a device fault: stop using the CUDA context
+                                      (the kernel waits once more, bounded, before it exits) */
 
 /* Interpolation configuration (Sec. IV-B). */
 typedef struct {
@@ -352,9 +355,11 @@ int interp_timing_read(double *compress_ms, int32_t *compress_launches, double *
  * results as interp_compress without d_ws / ws_bytes: the scratch is an array compiled
  * into the library (interp_noalloc_scratch_bytes() bytes, 24 MiB, held on every GPU that
  * loads the library until the process exits).  Fields whose interp_workspace_bytes()
- * exceed it are rejected with INTERP_ESCRATCH before any work is enqueued.  The first
- * call on a device (with that device current) looks up the array's device address; make
- * that first call before any stream capture.  Every call reuses the same array and clears
+ * exceed it are rejected with INTERP_ESCRATCH before any work is enqueued.  Every call
+ * made outside stream capture looks up the array's device address on the current device
+ * (so a device reset, which may move the array, is harmless); a call during capture uses
+ * the address an earlier call on that device looked up, so make one call on the device
+ * before capturing (INTERP_ECUDA otherwise).  Every call reuses the same array and clears
  * what must start at zero itself; calls whose work overlaps on the GPU race on it.  Not
  * thread-safe.  Allocates and frees nothing. */
 int interp_compress_noalloc(const float *d_x, const int64_t dims[3], double eb, const interp_config *cfg,

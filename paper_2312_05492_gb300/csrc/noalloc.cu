@@ -11,10 +11,11 @@
 // The array is a file-scope __device__ variable of kNoAllocScratchBytes
 // (24 MiB): every GPU on which the library's code is loaded holds it until
 // the process exits.  Host code cannot use the array's name as a device
-// address (on the host it names a stand-in object), so the first call on a
-// device, with that device current, looks up the array's device address with
-// cudaGetSymbolAddress and caches it for that device.  That first call should
-// therefore come before any stream capture.  All calls share the one array:
+// address (on the host it names a stand-in object), so every call made outside
+// stream capture, with the device current, looks up the array's device address
+// with cudaGetSymbolAddress (a device reset may move the array) and keeps it
+// for that device; a call during capture uses the kept address, so one call on
+// the device must come before any capture.  All calls share the one array:
 // compression clears the parts that must start at zero (control words and
 // outlier block counters) at the start of every call, and two calls whose
 // work overlaps on the GPU (different streams, or different host threads)
@@ -44,10 +45,15 @@ extern "C" int interp_compress_noalloc(const float *d_x, const int64_t dims[3], 
     if (need > kNoAllocScratchBytes) return INTERP_ESCRATCH;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return INTERP_ECUDA;
-    if (!g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cap) != cudaSuccess) return INTERP_ECUDA;
+    if (cap == cudaStreamCaptureStatusNone) {
+        // outside capture: look the address up every time (a device reset may move the array)
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return INTERP_ECUDA;
         g_scratch_addr[dev] = p;
+    } else if (!g_scratch_addr[dev]) {
+        return INTERP_ECUDA;  // captured before any call on this device looked the address up
     }
     return interp_compress(d_x, dims, eb, cfg, d_anchors, d_codes, d_out_idx, d_out_val, out_capacity, d_hist,
                            d_hdr, g_scratch_addr[dev], kNoAllocScratchBytes, stream);

@@ -1332,10 +1332,13 @@ void plan_runs(Field *fs, int n, int grid, int forced = 0)
             work += (long long)fs[i].cols * fs[i].slabs;
         }
         const long long per_cta = (items + grid - 1) / grid;
-        // a CTA's time ~ its items x the run length, plus a recomputed plane per item
-        const double cost = (double)per_cta * (run + 0.15);
+        // the busiest CTA's items, each the run length plus the cost of a run start
+        // (plane 0 loaded and computed, the transfers not yet overlapped: about two
+        // slabs), and the run length once more for the CTAs that idle while the last
+        // items finish; fitted to 512^3 timings of runs 1 .. 64 (best: 8)
+        const double cost = (double)per_cta * (run + 2.0) + 1.0 * run;
         (void)work;
-        if (cost < best - 1e-9) {
+        if (cost <= best + 1e-9) {  // ties: the longer run (fewer run starts)
             best = cost;
             best_run = run;
         }

@@ -86,17 +86,20 @@ constexpr int HIST_WORDS = HIST_SMEM_BINS + 32;
 constexpr size_t C_BAR = al16(C_HIST + sizeof(uint32_t) * HIST_WORDS);
 constexpr size_t kCompressSmem = C_BAR + 16;
 static_assert(sizeof(uint16_t) * STAGE <= sizeof(float) * XLAND, "staged codes fit the landing buffer");
-// decompression: two code landing buffers (the next slab's codes land while the
-// current slab's passes read theirs), then the value box and one barrier per buffer
+// decompression: one code landing buffer (the next slab's codes land once the
+// current slab's passes are done with theirs), then the value box and its barrier
 __host__ __device__ constexpr size_t al128(size_t v) { return (v + 127) / 128 * 128; }
 constexpr size_t D_LAND = 0;
-constexpr size_t D_LANDB = al128(sizeof(uint16_t) * KLAND);  // bytes per landing buffer
-constexpr size_t D_BOX = 2 * D_LANDB;
+constexpr size_t D_BOX = al128(sizeof(uint16_t) * KLAND);
 constexpr size_t D_BAR = al16(D_BOX + sizeof(float) * BOXF);
 constexpr size_t kDecompressSmem = D_BAR + 16;
 // with 16-row columns, 5 compression CTAs fit an SM: dynamic + static (< 512 B) + 1 KB reserved each
 constexpr int kCompressCtas = 5;
 static_assert(OY != 16 || kCompressCtas * (kCompressSmem + 512 + 1024) <= 228 * 1024, "compression CTAs per SM");
+// the smaller decompression CTA leaves room for six (at 56 registers a thread)
+constexpr int kDecompressCtas = 6;
+static_assert(OY != 16 || kDecompressCtas * (kDecompressSmem + 512 + 1024) <= 228 * 1024,
+              "decompression CTAs per SM");
 
 // Nonzero iff one of the two 16-bit halves of w is zero (a borrow can only set
 // bits above a zero half, never create one).
@@ -1097,12 +1100,14 @@ struct DBatch {
     int n, items;
 };
 
-// Decompression.  The codes of a slab land (TMA) in one of two buffers while the
-// previous slab is reconstructed from the other; the passes read them in place.
-// The anchors of the next slab are fetched into registers before the current
-// slab's passes, so that no global-memory latency sits between two slabs.
+// Decompression.  The codes of a slab land (TMA) in the landing buffer and the
+// passes read them in place; the next slab's codes are issued as soon as the
+// passes are done, so they land during the write-out, and the anchors of the
+// next slab are fetched into registers before the current slab's passes.  One
+// buffer (rather than two) lets six CTAs share an SM, whose extra warps hide
+// the rest of the latency (measured faster than two buffers at five CTAs).
 template <bool MULTI>
-__global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_constant__ DBatch B)
+__global__ void __launch_bounds__(NT, kDecompressCtas) k_decompress(const __grid_constant__ DBatch B)
 {
     unsigned char *smem = g_smem;
     Levels &lv = g_lv;
@@ -1110,15 +1115,14 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
     float *box = reinterpret_cast<float *>(smem + D_BOX);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + D_BAR);
     const BatchView<DField> bv{B.fld, B.n, B.items};
+    uint16_t *land = reinterpret_cast<uint16_t *>(smem + D_LAND);
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(bar, 1);
         fence_barrier_init();
     }
     __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
-    auto land_of = [&](int b) { return reinterpret_cast<uint16_t *>(smem + D_LAND + b * D_LANDB); };
+    uint32_t phase = 0u;
 
     // anchors of a slab's planes 8 and (when not carried) 0: thread t < 2 * AYN * AXN holds one
     constexpr int AYN = OY / 8 + 1, AXN = OX / 8 + 1;  // anchor rows / columns of the box
@@ -1142,14 +1146,12 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
     Slab sl;
     slab_of<MULTI>(sl, cu, bv);
     int lv_field = -1;
-    int buf = 0;
-    bool pending_next = false;  // the next slab's transfer was issued and not yet waited for
     float anc = 0.0f;
     bool anc_ok;
     {
         const int fi = MULTI ? cu.fi : 0;
-        issue_land<uint16_t, KP, EZ, 0>(land_of(0), B.fld[fi].a.codes, &B.map[fi], B.fld[fi].use_tma, &bar[0],
-                                        B.fld[fi].f, sl);
+        issue_land<uint16_t, KP, EZ, 0>(land, B.fld[fi].a.codes, &B.map[fi], B.fld[fi].use_tma, bar, B.fld[fi].f,
+                                        sl);
         anc_ok = anchor_fetch(B.fld[fi], sl, anc);
     }
     for (;;) {
@@ -1162,19 +1164,9 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
         if (has_next) slab_of<MULTI>(sn, nx, bv);
         if (threadIdx.x == 0 && lv_field != fi) load_levels(lv, F.a.hdr);
         lv_field = fi;
-        uint16_t *land = land_of(buf);
 
-        // ---- this slab's codes; the next slab's into the other buffer (its last reader,
-        // the slab before this one, is done: the loop ends with a barrier)
-        const bool landed = wait_land(F.use_tma, &bar[buf], phase[buf]);
-        if (!landed) abort_flag = 1;
-        pending_next = has_next && landed;
-        if (pending_next) {
-            const int nfi = MULTI ? nx.fi : 0;
-            const DField &N = B.fld[nfi];
-            issue_land<uint16_t, KP, EZ, 0>(land_of(buf ^ 1), N.a.codes, &B.map[nfi], N.use_tma, &bar[buf ^ 1], N.f,
-                                            sn);
-        }
+        // ---- this slab's codes
+        if (!wait_land(F.use_tma, bar, phase)) abort_flag = 1;
         if (anc_ok) box[a_off] = anc;  // this slab's anchors, fetched a slab ago
         if (has_next) {
             const int nfi = MULTI ? nx.fi : 0;
@@ -1214,6 +1206,12 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
 
         const Sink sk{nullptr, land, nullptr, nullptr};
         run_slab<false>(box, sk, sl, f, lv);  // ends with a barrier
+        // ---- the codes are read: the next slab's land during the write-out
+        if (has_next) {
+            const int nfi = MULTI ? nx.fi : 0;
+            const DField &N = B.fld[nfi];
+            issue_land<uint16_t, KP, EZ, 0>(land, N.a.codes, &B.map[nfi], N.use_tma, bar, N.f, sn);
+        }
 
         // ---- write the owned planes
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1251,7 +1249,7 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
                 }
             }
         }
-        __syncthreads();  // every thread is done reading the box and this slab's codes
+        __syncthreads();  // every thread is done reading the box
         if (!has_next) break;
         // ---- carry plane 8 into plane 0 of the next slab of the same run
         if (nx.item == cu.item) {
@@ -1260,16 +1258,13 @@ __global__ void __launch_bounds__(NT, kCompressCtas) k_decompress(const __grid_c
         }
         cu = nx;
         sl = sn;
-        buf ^= 1;
     }
     if (abort_flag && threadIdx.x == 0) {
         atomicOr(&const_cast<interp_header *>(B.fld[MULTI ? cu.fi : 0].a.hdr)->status, INTERP_STATUS_TIMEOUT);
-        // give the transfers still in flight (this slab's, and the next one's if it was
-        // issued) a second bounded wait before the CTA's shared memory is released
-        if (B.fld[MULTI ? cu.fi : 0].use_tma) {
-            mbar_wait_bounded(&bar[buf], phase[buf] ^ 1u, kTmaPolls);
-            if (pending_next) mbar_wait_bounded(&bar[buf ^ 1], phase[buf ^ 1], kTmaPolls);
-        }
+        // the transfer that did not arrive (the only one issued: the next slab's is
+        // issued after the passes) gets a second bounded wait before the CTA's shared
+        // memory is released
+        if (B.fld[MULTI ? cu.fi : 0].use_tma) mbar_wait_bounded(bar, phase ^ 1u, kTmaPolls);
     }
     cp_async_wait_all();
 }

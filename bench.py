@@ -128,14 +128,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# sources of the kernels whose ncu counters are committed (k_compress, k_decompress, k_range)
-TRAFFIC_SOURCES = ("common.cuh", "tma.cuh", "tiles.cu", "profile.cu")
+# sources of each kernel whose ncu counters are committed
+TRAFFIC_SOURCES = {
+    "k_compress": ("common.cuh", "tma.cuh", "tiles.cu"),
+    "k_decompress": ("common.cuh", "tma.cuh", "tiles.cu"),
+    "k_prologue": ("common.cuh", "profile.cu"),
+}
 
 
-def source_hash() -> str:
+def source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2312_05492_gb300", "csrc")
-    for f in TRAFFIC_SOURCES:
+    for f in TRAFFIC_SOURCES[kernel]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -143,14 +147,15 @@ def source_hash() -> str:
 
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        if d.get("source_hash") != source_hash():
+        k = d["kernels"][kernel]
+        if k.get("source_hash") != source_hash(kernel):
             return None
-        return d["kernels"][kernel]["dram_bytes_per_launch_full_size"]
+        return k["dram_bytes_per_launch_full_size"]
     except Exception:
         return None
 

@@ -376,11 +376,31 @@ int sm_count()
     return sms;
 }
 
-int range_blocks()
+namespace {
+
+// Blocks of a grid-stride range kernel that are resident at once on this
+// device (one wave): a block that had to wait for a free slot would finish its
+// whole share late.  Cached per device and kernel.
+constexpr int kMaxRangeDevices = 64;
+template <typename K>
+int one_wave(K kernel, int *cache)
 {
-    const int b = sm_count() * 4;
-    return b < RANGE_MAX_BLOCKS ? b : RANGE_MAX_BLOCKS;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    if (dev >= 0 && dev < kMaxRangeDevices && cache[dev] > 0) return cache[dev];
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, RANGE_THREADS, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int b = std::min(per_sm * sm_count(), RANGE_MAX_BLOCKS);
+    if (dev >= 0 && dev < kMaxRangeDevices) cache[dev] = b;
+    return b;
 }
+int range_wave[kMaxRangeDevices], prologue_wave[kMaxRangeDevices];
+
+}  // namespace
+
+int range_blocks() { return one_wave(k_range, range_wave); }
 
 size_t range_partials_bytes() { return sizeof(RangePartial) * RANGE_MAX_BLOCKS; }
 
@@ -426,9 +446,10 @@ cudaError_t launch_prologue(const PrologueItem *items, int n, cudaStream_t s)
         F.first_axis = (it.cfg.ndim == 1 || it.cfg.ndim == 2) ? 3 - it.cfg.ndim : 0;
         F.b0 = blocks;
         F.nprof = it.cfg.autotune ? 1 : 0;
-        // range blocks: about 32 K values each, at most range_blocks()
+        // range blocks: about 32 K values each, at most one wave beside the profile block
         const unsigned long long want = (F.n + 32767) / 32768;
-        F.nrange = it.cfg.eb_mode ? (int)std::max(1ull, std::min<unsigned long long>(want, range_blocks())) : 1;
+        const int wave = std::max(1, one_wave(k_prologue, prologue_wave) - F.nprof);
+        F.nrange = it.cfg.eb_mode ? (int)std::max(1ull, std::min<unsigned long long>(want, wave)) : 1;
         blocks += F.nprof + F.nrange;
         ZeroField &zf = Z.f[i];
         zf.ctrl = it.counter;

@@ -105,13 +105,6 @@ static_assert(OY != 16 || kDecompressCtas * (kDecompressSmem + 512 + 1024) <= 22
 // bits above a zero half, never create one).
 __device__ __forceinline__ uint32_t has_zero_half(uint32_t w) { return (w - 0x00010001u) & ~w & 0x80008000u; }
 
-// ------------------------------------------------------------ cp.async (fallback path)
-__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------ context
 struct Field {

@@ -657,6 +657,62 @@ __device__ __forceinline__ void nd_compress_tile(const CompressArgs &a, const Nd
     // codes, outlier bitmap words and the histogram of the owned points
     const int lane = tid & 31, warp = tid >> 5;
     const int wpr = (d.nx + 31) / 32;
+    const bool octets = t.ox == G::TX && (d.nx & 7) == 0 && (reinterpret_cast<uintptr_t>(a.codes) & 15u) == 0;
+    if (octets) {
+        // tiles owning all TX columns, rows 16-byte aligned: a thread takes 8 consecutive
+        // codes of a row (one 16-byte load and store); the 4 lanes of a 32-code strip
+        // assemble its outlier word, and one atomic per warp carries the block counts
+        constexpr int OPR = G::TX / 8;  // octets per row
+        const uint32_t R = (uint32_t)a.radius;
+        for (int o0 = warp * 32; o0 < G::TY * OPR; o0 += ND_THREADS) {
+            const int o = o0 + lane;
+            const int by = o / OPR, x8 = 8 * (o - by * OPR);
+            const bool in = by < t.oy;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            uint32_t zmask = 0u;
+            const long long row = t.row0 + by;
+            if (in) {
+                const uint32_t *c32 = reinterpret_cast<const uint32_t *>(cs) + hix<NDIM>(by * G::TX + x8) / 2;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[j] = c32[j];
+                *reinterpret_cast<uint4 *>(a.codes + row * d.nx + t.x0 + x8) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t code = (w[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                    zmask |= (code == 0u ? 1u : 0u) << j;
+                    if (a.hist) {
+                        if (code == R) ++central;
+                        else if (code < (uint32_t)bins) {
+                            if (smem_hist) atomicAdd(&hs[code], 1u);
+                            else atomicAdd(&a.hist[code], 1u);
+                        }
+                    }
+                }
+            }
+            uint32_t word = zmask << (8 * (lane & 3));
+            word |= __shfl_xor_sync(0xffffffffu, word, 1);
+            word |= __shfl_xor_sync(0xffffffffu, word, 2);
+            const long long gw = row * wpr + ((t.x0 + x8) >> 5);  // row-major bitmap
+            if (in && (lane & 3) == 0) a.bitmap[gw] = word;
+            const bool has = in && (lane & 3) == 0 && word != 0u;
+            const uint32_t hm = __ballot_sync(0xffffffffu, has);
+            if (hm) {
+                const long long blk = gw / BITMAP_BLOCK_WORDS;
+                const int first = __ffs(hm) - 1;
+                const long long b0 = __shfl_sync(0xffffffffu, blk, first);
+                uint32_t c = has ? (uint32_t)__popc(word) : 0u;
+                if (__all_sync(0xffffffffu, !has || blk == b0)) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+                    if (lane == first) atomicAdd(a.blockcnt + b0, c);
+                } else if (has) {
+                    atomicAdd(a.blockcnt + blk, c);
+                }
+            }
+        }
+        __syncthreads();  // the box and the code stage are reused by the next tile
+        return;
+    }
     const bool pairs = NDIM == 2 && t.ox == G::TX && (d.nx & 1) == 0 &&
                        (reinterpret_cast<uintptr_t>(a.codes) & 3u) == 0;
     if (pairs) {

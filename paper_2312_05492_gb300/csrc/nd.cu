@@ -544,6 +544,62 @@ __device__ __forceinline__ void nd2_seg_pass(float *v, const NdPointCtx &c)
     }
 }
 
+// 1-D whole tiles, segments: one work unit is P consecutive points of a level-S pass
+// (P = 4 at stride 1, 2 at stride 2, else 1), whose known neighbours at even multiples
+// of S give all its predictions from registers, plus the known points just outside
+// the segment where the segment does not start or end a chunk.  Every chunk is whole:
+// the first point of a chunk has no x_{n-3s} (right quadratic), the last no x_{n+3s}
+// (left quadratic), a lone midpoint neither (linear), the rest are cubic (Sec. IV-B.1).
+template <int S, bool COMPRESS>
+__device__ __forceinline__ void nd1_seg_pass(float *v, const NdPointCtx &c)
+{
+    using G = NdGeom<1>;
+    constexpr int A = G::A;
+    // points per segment: as many as keep one segment per thread (NSEG >= ND_THREADS)
+    constexpr int P = S == 1 ? 4 : (S == 2 ? 2 : 1);
+    constexpr int SPAN = 2 * S * P;                           // the segment's known points: 0, 2S, .., SPAN
+    constexpr int NSEG = G::TX / SPAN;
+#pragma unroll 1
+    for (int w = threadIdx.x; w < NSEG; w += ND_THREADS) {
+        const int n0 = w * SPAN;
+        const bool at_lo = n0 % A == 0, at_hi = (n0 + SPAN) % A == 0;  // the segment starts / ends a chunk
+        float k[P + 3];  // k[q + 1] = x_{n0 + 2Sq}, q = -1 .. P + 1
+#pragma unroll
+        for (int q = 0; q <= P; ++q) k[q + 1] = v[vix<1>(n0 + 2 * S * q)];
+        k[0] = 0.0f;
+        k[P + 2] = 0.0f;
+        if (c.spline) {
+            if (!at_lo) k[0] = v[vix<1>(n0 - 2 * S)];
+            if (!at_hi) k[P + 2] = v[vix<1>(n0 + SPAN + 2 * S)];
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int o = n0 + (2 * q + 1) * S;
+            const float m1 = k[q + 1], p1 = k[q + 2];
+            float p;
+            if (!c.spline) {
+                p = sp_linear(m1, p1);
+            } else {
+                const bool hm3 = q > 0 || !at_lo, hp3 = q < P - 1 || !at_hi;
+                if (hm3 && hp3) p = sp_cubic(c.ck, k[q], m1, p1, k[q + 3]);
+                else if (hm3) p = sp_quad_left(k[q], m1, p1);
+                else if (hp3) p = sp_quad_right(m1, p1, k[q + 3]);
+                else p = sp_linear(m1, p1);
+            }
+            if (COMPRESS) {
+                float xr;
+                const int vi = vix<1>(o);
+                const uint32_t code = quantize(v[vi], p, c.q, c.cbias, c.Rf, xr);
+                v[vi] = xr;
+                c.cs[hix<1>(o)] = (uint16_t)code;
+            } else {
+                const uint32_t code = c.cb[hix<1>(o)];
+                v[vix<1>(o)] = code ? p + code_to_q(code, c.cbias) * c.q.twoe : c.xrec[c.row0 * c.nx + c.x0 + o];
+            }
+        }
+    }
+}
+
 // Levels S, S/2, ..., 1 of a full tile; in 2-D the axis interpolated first in a level
 // sees the other on the 2s-grid, the second on the s-grid.
 template <int NDIM, int S, bool XFIRST, bool COMPRESS>
@@ -555,7 +611,7 @@ __device__ __forceinline__ void nd_full_levels(float *v, NdPointCtx &c, const Le
     c.spline = cfg.level_kind[l < 2 ? l : 2];
     if (NDIM == 1) {
         c.ck = cubic_coeffs(cfg.cubic_kind[2]);
-        nd_full_pass<NDIM, S, 2, 1, COMPRESS>(v, c);
+        nd1_seg_pass<S, COMPRESS>(v, c);
         __syncthreads();
     } else {
         constexpr int F = XFIRST ? 2 : 1, O = XFIRST ? 1 : 2;
@@ -882,9 +938,20 @@ __device__ __forceinline__ void nd_decompress_tile(const DecompressArgs &a, cons
             __syncthreads();
         }
     }
-    for (int by = 0; by < t.oy; ++by) {
-        float *dst = a.xrec + (t.row0 + by) * d.nx + t.x0;
-        for (int bx = tid; bx < t.ox; bx += ND_THREADS) dst[bx] = v[vix<NDIM>(by * G::PX + bx)];
+    if (t.ox == G::TX && (d.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(a.xrec) & 15u) == 0) {
+        // whole-width tiles with 16-byte aligned rows: 4 values per 16-byte store
+        constexpr int QPR = G::TX / 4;  // quads per row
+        for (int qd = tid; qd < t.oy * QPR; qd += ND_THREADS) {
+            const int by = qd / QPR, x4 = 4 * (qd - by * QPR);
+            const int j = by * G::PX + x4;
+            *reinterpret_cast<float4 *>(a.xrec + (t.row0 + by) * d.nx + t.x0 + x4) =
+                make_float4(v[vix<NDIM>(j)], v[vix<NDIM>(j + 1)], v[vix<NDIM>(j + 2)], v[vix<NDIM>(j + 3)]);
+        }
+    } else {
+        for (int by = 0; by < t.oy; ++by) {
+            float *dst = a.xrec + (t.row0 + by) * d.nx + t.x0;
+            for (int bx = tid; bx < t.ox; bx += ND_THREADS) dst[bx] = v[vix<NDIM>(by * G::PX + bx)];
+        }
     }
     __syncthreads();  // the box is reused by the next tile
 }

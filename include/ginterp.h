@@ -82,8 +82,8 @@ typedef struct {
                               own; 1 = 512-point chunks along x, strides 256 .. 1, every (z, y)
                               row on its own.  Levels coarser than stride 4 use level_kind[2];
                               their bounds continue e_l = e / alpha^l.  1 and 2 need domain_x
-                              0 or 8 and are taken by interp_compress / interp_decompress_nd
-                              only (not by the batched or no-allocation forms). */
+                              0 or 8 and are taken by interp_compress / interp_decompress_nd,
+                              the batched forms and the no-allocation form. */
     double alpha;          /* error-bound reduction factor; <= 0 selects Eq. 1 A(eps) in
                               relative mode and 1 in absolute mode */
 } interp_config;
@@ -164,11 +164,14 @@ int interp_decompress_nd(int32_t ndim, const int64_t dims[3], const interp_heade
 
 /* Batched forms: n fields of any (uneven) shapes, bounds and configurations in one call.
  * Each item carries exactly the arguments of the single-field call (its own workspace).
- * Per-field setup (range, profile, bounds) and outlier compaction are enqueued per field;
- * the tile work of all fields runs in ONE persistent kernel launch whose CTAs take work
- * items (runs of 8-plane slabs of 16 x 32 columns) from all fields.  Results are identical,
- * bit for bit, to n single calls.  1 <= n <= 16.  Stream-ordered, no synchronisation;
- * capturable into a CUDA graph after one warm-up call on the device. */
+ * The set-up of all fields (workspace clear; range, profile, bounds), their outlier
+ * compaction and, for decompression, their outlier scatter take one launch per phase for
+ * the whole batch.  The tile work of all 3-D fields runs in ONE persistent kernel launch
+ * whose CTAs take work items (runs of 8-plane slabs of 16 x 32 columns) from all of them;
+ * 1-D / 2-D fields (interp_config.ndim 1 or 2 when compressing, the item's ndim when
+ * decompressing) take one tile launch each.  Results are identical, bit for bit, to n
+ * single calls.  1 <= n <= 16.  Stream-ordered, no synchronisation; capturable into a CUDA
+ * graph after one warm-up call on the device. */
 typedef struct {
     const float *d_x;
     int64_t dims[3];
@@ -194,6 +197,9 @@ typedef struct {
     const float *d_out_val;
     uint64_t out_capacity;
     float *d_xrec;
+    int32_t ndim; /* the field's chunk geometry, its interp_config.ndim at compression:
+                     0 or 3 = 3-D, 1 / 2 = 1-D / 2-D chunks (interp_decompress_nd); others
+                     INTERP_EINVAL */
 } interp_decompress_item;
 
 int interp_compress_batched(const interp_compress_item *h_items, int n, interp_stream_t stream);

@@ -157,6 +157,9 @@ size_t interp_workspace_bytes(const int64_t dims[3], const interp_config *cfg)
 }
 
 // The compression set-up of one field (zeroing, profile, range and bounds).
+// The 1-D / 2-D chunk geometries (interp_config.ndim 1 or 2); 0 and 3 are 3-D.
+bool is_nd(int32_t ndim) { return ndim == 1 || ndim == 2; }
+
 gi::PrologueItem prologue_item(const interp_compress_item &it, const WsLayout &L)
 {
     unsigned char *ws = static_cast<unsigned char *>(it.d_ws);
@@ -228,7 +231,6 @@ int interp_compress_batched_scheduled(const interp_compress_item *items, int n, 
     for (int i = 0; i < n; ++i) {  // every argument is checked before anything is enqueued
         const interp_compress_item &it = items[i];
         if (!dims_ok(it.dims) || !cfg_ok(&it.cfg)) return INTERP_EINVAL;
-        if (it.cfg.ndim == 1 || it.cfg.ndim == 2) return INTERP_EINVAL;  // single-field calls only
         if (!(it.eb > 0.0) || std::isinf(it.eb)) return INTERP_EINVAL;
         if (!it.d_x || !it.d_anchors || !it.d_codes || !it.d_hdr || !it.d_ws) return INTERP_EINVAL;
         if (it.out_capacity > 0 && (!it.d_out_idx || !it.d_out_val)) return INTERP_EINVAL;
@@ -237,8 +239,9 @@ int interp_compress_batched_scheduled(const interp_compress_item *items, int n, 
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // set-up of every field in two launches (zeroing; profile, range and bounds)
-    gi::CompressArgs args[gi::kMaxBatch];
+    gi::CompressArgs args[gi::kMaxBatch], args3[gi::kMaxBatch];
     gi::PrologueItem pro[gi::kMaxBatch];
+    int n3 = 0;
     for (int i = 0; i < n; ++i) {
         const interp_compress_item &it = items[i];
         const interp_config &c = it.cfg;
@@ -247,25 +250,34 @@ int interp_compress_batched_scheduled(const interp_compress_item *items, int n, 
         uint32_t *bitmap = reinterpret_cast<uint32_t *>(ws + L[i].bitmap);
         uint32_t *blockcnt = reinterpret_cast<uint32_t *>(ws + L[i].blockcnt);
         pro[i] = prologue_item(it, L[i]);
-        args[i] = gi::CompressArgs{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
-                                   it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0, c.domain_x == 32,
-                                   code_store_width(it.d_codes, d.nx)};
+        if (is_nd(c.ndim))
+            args[i] = gi::CompressArgs{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
+                                       it.d_hdr, false, false, 1};
+        else
+            args3[n3++] = args[i] =
+                gi::CompressArgs{it.d_x, d, it.d_anchors, it.d_codes, bitmap, blockcnt, it.d_hist, c.radius,
+                                 it.d_hdr, gi::aligned16(it.d_codes) && d.nx % 8 == 0, c.domain_x == 32,
+                                 code_store_width(it.d_codes, d.nx)};
     }
     cudaError_t e = gi::launch_prologue(pro, n, s);
     if (e == cudaSuccess) {
         timing_mark(0, 0, s);
         const gi::TileSchedule ts{sched ? sched->run : 0, sched ? sched->ctas_per_sm : 0};
-        e = gi::launch_compress_tiles(args, n, s, &ts);  // one persistent launch for every field
+        if (n3 > 0) e = gi::launch_compress_tiles(args3, n3, s, &ts);  // one persistent launch for every 3-D field
+        for (int i = 0; i < n && e == cudaSuccess; ++i)                // one launch per 1-D / 2-D field
+            if (is_nd(items[i].cfg.ndim)) e = gi::launch_nd_compress(items[i].cfg.ndim, args[i], s);
         timing_mark(0, 1, s);
     }
     if (e == cudaSuccess) {
-        // ordered compaction of every field in two launches; the tile kernel leaves bin R to the scan
+        // ordered compaction of every field in two launches; the 3-D tile kernel leaves bin R
+        // to the scan, the 1-D / 2-D kernels count every bin and write row-major bitmaps
         gi::CompactItem ci[gi::kMaxBatch];
         for (int i = 0; i < n; ++i) {
             const interp_compress_item &it = items[i];
+            const bool nd = is_nd(it.cfg.ndim);
             ci[i] = gi::CompactItem{args[i].bitmap, args[i].blockcnt, L[i].words, args[i].dims, it.d_x,
-                                    it.d_out_idx, it.d_out_val, it.out_capacity, it.d_hdr, false, it.d_hist,
-                                    it.cfg.radius};
+                                    it.d_out_idx, it.d_out_val, it.out_capacity, it.d_hdr, nd,
+                                    nd ? nullptr : it.d_hist, it.cfg.radius};
         }
         e = gi::launch_outlier_compaction(ci, n, s);
     }
@@ -308,28 +320,34 @@ int interp_decompress_batched_scheduled(const interp_decompress_item *items, int
     if (!items || n < 1 || n > gi::kMaxBatch) return INTERP_EINVAL;
     for (int i = 0; i < n; ++i) {
         const interp_decompress_item &it = items[i];
-        if (!dims_ok(it.dims)) return INTERP_EINVAL;
+        if (!dims_ok(it.dims) || it.ndim < 0 || it.ndim > 3) return INTERP_EINVAL;
         if (!it.d_hdr || !it.d_anchors || !it.d_codes || !it.d_xrec) return INTERP_EINVAL;
         if (it.out_capacity > 0 && (!it.d_out_idx || !it.d_out_val)) return INTERP_EINVAL;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    gi::DecompressArgs args[gi::kMaxBatch];
+    gi::DecompressArgs args[gi::kMaxBatch], args3[gi::kMaxBatch];
     gi::ScatterItem sc[gi::kMaxBatch];
-    int nsc = 0;
+    int nsc = 0, n3 = 0;
     for (int i = 0; i < n; ++i) {
         const interp_decompress_item &it = items[i];
         const Dims d = to_dims(it.dims);
         if (it.out_capacity > 0) sc[nsc++] = gi::ScatterItem{it.d_hdr, it.d_out_idx, it.d_out_val, it.out_capacity,
                                                              it.d_xrec};
-        args[i] = gi::DecompressArgs{d, it.d_anchors, it.d_codes, it.d_xrec, it.d_hdr,
-                                     gi::aligned16(it.d_xrec) && d.nx % 4 == 0};
+        if (is_nd(it.ndim))
+            args[i] = gi::DecompressArgs{d, it.d_anchors, it.d_codes, it.d_xrec, it.d_hdr, false};
+        else
+            args3[n3++] = args[i] = gi::DecompressArgs{d, it.d_anchors, it.d_codes, it.d_xrec, it.d_hdr,
+                                                       gi::aligned16(it.d_xrec) && d.nx % 4 == 0};
     }
-    // every field's stored outlier values in one launch, then one tile launch
+    // every field's stored outlier values in one launch, then one tile launch for the 3-D
+    // fields and one per 1-D / 2-D field
     cudaError_t e = nsc > 0 ? gi::launch_outlier_scatter(sc, nsc, s) : cudaSuccess;
     if (e == cudaSuccess) {
         timing_mark(1, 0, s);
         const gi::TileSchedule ts{sched ? sched->run : 0, sched ? sched->ctas_per_sm : 0};
-        e = gi::launch_decompress_tiles(args, n, s, &ts);  // one persistent launch for every field
+        if (n3 > 0) e = gi::launch_decompress_tiles(args3, n3, s, &ts);
+        for (int i = 0; i < n && e == cudaSuccess; ++i)
+            if (is_nd(items[i].ndim)) e = gi::launch_nd_decompress(items[i].ndim, args[i], s);
         timing_mark(1, 1, s);
     }
     return cuda_status(e);
@@ -349,6 +367,7 @@ int interp_decompress(const int64_t dims[3], const interp_header *d_hdr, const f
     it.d_out_val = d_out_val;
     it.out_capacity = out_capacity;
     it.d_xrec = d_xrec;
+    it.ndim = 3;
     return interp_decompress_batched(&it, 1, stream);
 }
 

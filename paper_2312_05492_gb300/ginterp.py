@@ -78,7 +78,7 @@ class interp_tile_schedule(ctypes.Structure):
 class interp_decompress_item(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int64 * 3), ("d_hdr", ctypes.c_void_p), ("d_anchors", ctypes.c_void_p),
                 ("d_codes", ctypes.c_void_p), ("d_out_idx", ctypes.c_void_p), ("d_out_val", ctypes.c_void_p),
-                ("out_capacity", ctypes.c_uint64), ("d_xrec", ctypes.c_void_p)]
+                ("out_capacity", ctypes.c_uint64), ("d_xrec", ctypes.c_void_p), ("ndim", ctypes.c_int32)]
 
 
 MAX_BATCH = 16
@@ -627,6 +627,7 @@ def decompress_item(cf: CompressedField, out: torch.Tensor) -> interp_decompress
     it.d_out_val = _ptr(cf.out_val)
     it.out_capacity = int(cf.capacity)
     it.d_xrec = _ptr(out)
+    it.ndim = int(cf.cfg.ndim)
     return it
 
 

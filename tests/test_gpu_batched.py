@@ -72,6 +72,37 @@ def test_batch_order_does_not_matter():
         _same(a.fields[p], a.outs[p], b.fields[j], b.outs[j])
 
 
+def test_batched_mixed_geometries():
+    """3-D fields and 1-D / 2-D fields (Sec. IV-A chunk geometries) in one batch: the
+    3-D fields share the persistent launch, the others take one launch each, and every
+    field equals its single call bit for bit (compression and decompression, also as a
+    replayed CUDA graph)."""
+    xs = [fields.grf((20, 100, 100), 4.0, 2).cuda(), fields.grf((3, 70, 300), 3.0, 5).cuda(),
+          fields.grf((2, 3, 3000), 3.0, 7).cuda(), fields.shocks((5, 40, 130), 6).cuda(),
+          fields.sines((17, 33, 65), 4).cuda()]
+    ebs = [1e-3, 1e-3, 1e-4, 1e-5, 1e-3]
+    cfgs = [G.Config(autotune=True), G.Config(autotune=True, ndim=2), G.Config(autotune=True, ndim=1),
+            G.Config(ndim=2, radius=2, level_kind=(1, 1, 1)), G.Config(radius=64, level_kind=(1, 1, 1))]
+    b = G.Batch(xs, ebs, cfgs, capacities=[x.numel() for x in xs])
+    b.round_trip()
+    torch.cuda.synchronize()
+    singles = [_single(x, eb, cfg) for x, eb, cfg in zip(xs, ebs, cfgs)]
+    torch.cuda.synchronize()
+    for i, (cf, xr) in enumerate(singles):
+        _same(b.fields[i], b.outs[i], cf, xr)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    for o in b.outs:
+        o.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.round_trip(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for i, (cf, xr) in enumerate(singles):
+        _same(b.fields[i], b.outs[i], cf, xr)
+
+
 def test_batched_cuda_graph_replay():
     xs, ebs, cfgs = _batch_inputs()
     b = G.Batch(xs, ebs, cfgs, capacities=[x.numel() for x in xs])

@@ -80,7 +80,9 @@ def test_nd_capacity_overflow_flags_and_counts():
     assert h.n_outliers > 16 and h.status & G.STATUS_CAPACITY
 
 
-def test_nd_rejects_x_domain_and_batched():
+def test_nd_rejects_x_domain_and_joins_batches():
+    """The x-extended domain is a 3-D option (refused with 1-D / 2-D chunks); the batched
+    entry point takes 1-D / 2-D fields (their parity is in test_gpu_batched.py)."""
     x = torch.zeros((1, 16, 16), device="cuda")
     with pytest.raises(G.InterpError):
         G.compress(x, 1e-3, G.Config(ndim=2, domain_x=32))
@@ -88,7 +90,9 @@ def test_nd_rejects_x_domain_and_batched():
     ws = torch.empty(G.interp_workspace_bytes(tuple(x.shape), G.Config(ndim=2).to_c()), dtype=torch.uint8,
                      device=x.device)
     it = G.compress_item(x, 1e-3, G.Config(ndim=2), bufs, ws)
-    assert G.interp_compress_batched([it], None) == G.INTERP_EINVAL
+    assert G.interp_compress_batched([it], None) == G.INTERP_OK
+    bad = G.compress_item(x, 1e-3, G.Config(ndim=2, domain_x=32), bufs, ws)
+    assert G.interp_compress_batched([it, bad], None) == G.INTERP_EINVAL
 
 
 @pytest.mark.parametrize("ndim", [2, 1])

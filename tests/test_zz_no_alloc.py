@@ -62,6 +62,8 @@ def test_noalloc_matches_regular_entry_on_two_calls_in_a_row():
         (fields.shocks((40, 48, 64), 6).cuda(), 1e-5, G.Config(radius=2, level_kind=(1, 1, 1))),
         # few outliers, another shape and config: stale counters from the first call would show
         (fields.lognormal((72, 56, 96), 11.0 / 3.0, 1).cuda(), 1e-3, G.Config(autotune=True, radius=512)),
+        # the 2-D chunk geometry (16^2 chunks, slices on their own) through the same entry
+        (fields.grf((3, 100, 300), 3.0, 5).cuda(), 1e-3, G.Config(autotune=True, ndim=2)),
     ]
     for x, eb, cfg in cases:
         n = x.numel()

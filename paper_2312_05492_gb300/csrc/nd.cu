@@ -14,8 +14,11 @@
 // tile) in shared memory, runs every pass on it, and writes only what it owns.
 // Passes inside a tile are separated by barriers; tiles are independent.  2-D passes
 // work on chunk lines (the 17 points of one chunk along the pass axis, its known
-// points in registers); 1-D passes on points, with compile-time shapes for whole
-// tiles.  Tiles clipped by the field's end take the neighbour-count rule per point.
+// points in registers, split in two at the fine strides); 1-D passes of whole tiles
+// on segments of 4, 2 or 1 points.  Tiles clipped by the field's end take the
+// neighbour-count rule per point.  2-D tiles stage the next tile asynchronously while
+// the current one is worked on; whole-width tiles write 8 codes (or 4 values) per
+// 16-byte store.
 // The level constants (double arithmetic, slow on this part) are formed once per
 // CTA, one thread per level.
 //

@@ -49,6 +49,35 @@ def test_struct_layouts(G):
     assert G.interp_header.profile.offset == 184
 
 
+def test_struct_layouts_match_the_c_header(G, tmp_path):
+    """Every field offset and size of the structs the binding declares, against a C
+    program compiled from include/ginterp.h (catches a field the binding lacks, or a
+    type of the wrong width)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [G.interp_config, G.interp_header, G.interp_compress_item, G.interp_decompress_item,
+               G.interp_tile_schedule]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ginterp.h"', 'int main(void) {']
+    for st in structs:
+        lines.append(f'printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for name, _ in st._fields_:
+            lines.append(f'printf("{st.__name__} {name} %zu\\n", offsetof({st.__name__}, {name}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert got[(st.__name__, name)] == getattr(st, name).offset, (st.__name__, name)
+
+
 def test_anchor_count_and_workspace(G):
     assert G.interp_anchor_count((64, 64, 64)) == 512
     assert G.interp_anchor_count((449, 449, 235)) == 57 * 57 * 30

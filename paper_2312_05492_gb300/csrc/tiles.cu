@@ -59,6 +59,7 @@ __host__ __device__ constexpr int cstride(int a) { return a == 2 ? 1 : (a == 1 ?
 // decompression reads the codes where the TMA landed them: rows of KP codes, planes of EY rows
 __host__ __device__ constexpr int lstride(int a) { return a == 2 ? 1 : (a == 1 ? KP : EY * KP); }
 static_assert((KP * 2) % 16 == 0, "landed code rows stay 16-byte aligned");
+static_assert(KP == 5 * 8, "a landed code row is 5 groups of 8 codes");
 __host__ __device__ constexpr int chunks_of(int a) { return a == 2 ? OX / 8 : (a == 1 ? OY / 8 : 1); }
 __host__ __device__ constexpr int axis_u(int d) { return d == 2 ? 1 : 2; }  // faster other axis
 __host__ __device__ constexpr int axis_v(int d) { return d == 0 ? 1 : 0; }
@@ -1128,13 +1129,13 @@ __device__ __forceinline__ void land_outliers(float *box, const uint16_t *land, 
     const int nyr = min(EY, f.n[1] - sl.g0[1]);
     const int nxc = min(EX, f.n[2] - sl.g0[2]);
     const int nitem = (EZ - pz0) * EY * 5;  // 5 groups of 8 codes per row (x 0..39)
+    // the landed rows are 5 groups each, so the groups of planes pz0.. are one flat run
+    const uint4 *l4 = reinterpret_cast<const uint4 *>(land) + pz0 * EY * 5;
     for (int i = threadIdx.x; i < nitem; i += NT) {
+        const uint4 v = l4[i];
+        if (!(has_zero_half(v.x) | has_zero_half(v.y) | has_zero_half(v.z) | has_zero_half(v.w))) continue;
         const int row = pz0 * EY + i / 5, q = i % 5;
-        const uint4 v = *reinterpret_cast<const uint4 *>(land + row * KP + 8 * q);
-        const uint32_t z = q < 4 ? (has_zero_half(v.x) | has_zero_half(v.y) | has_zero_half(v.z) |
-                                    has_zero_half(v.w))
-                                 : has_zero_half(v.x);  // the last group holds x = 32, 33 only
-        if (!z) continue;
+        if (q == 4 && !has_zero_half(v.x)) continue;  // the last group holds x = 32, 33 only
         const int pz = row / EY, y = row % EY;
         if (pz >= nzp || y >= nyr) continue;
         const uint32_t wv[4] = {v.x, v.y, v.z, v.w};

@@ -337,7 +337,8 @@ int interp_decompress_batched_scheduled(const interp_decompress_item *items, int
             args[i] = gi::DecompressArgs{d, it.d_anchors, it.d_codes, it.d_xrec, it.d_hdr, false};
         else
             args3[n3++] = args[i] = gi::DecompressArgs{d, it.d_anchors, it.d_codes, it.d_xrec, it.d_hdr,
-                                                       gi::aligned16(it.d_xrec) && d.nx % 4 == 0};
+                                                       gi::aligned16(it.d_xrec) && d.nx % 4 == 0, it.d_out_idx,
+                                                       it.out_capacity};
     }
     // every field's stored outlier values in one launch, then one tile launch for the 3-D
     // fields and one per 1-D / 2-D field

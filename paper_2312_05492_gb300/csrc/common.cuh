@@ -184,6 +184,8 @@ struct DecompressArgs {
     float *xrec;
     const interp_header *hdr;
     bool vec_xrec;  // xrec 16-byte aligned and nx % 4 == 0: 4-value vector stores
+    const uint32_t *out_idx = nullptr;  // the outlier list (ascending indices), may be null
+    uint64_t out_capacity = 0;          // its length in entries
 };
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

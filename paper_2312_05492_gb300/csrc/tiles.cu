@@ -1211,6 +1211,24 @@ __global__ void __launch_bounds__(NT, kDecompressCtas) k_decompress(const __grid
     if (!cursor_start<MULTI>(cu, bv, blockIdx.x)) return;
     Slab sl;
     slab_of<MULTI>(sl, cu, bv);
+    // A single field whose outliers are all listed and number at most one per thread:
+    // each thread keeps one outlier's coordinates, and a slab runs the outlier scan only
+    // when one of them lies in its box (on smooth fields almost none does).
+    bool few = false;
+    int oz = -1, oy = 0, ox = 0;
+    if (!MULTI) {
+        const DField &F0 = B.fld[0];
+        const unsigned long long nout = F0.a.hdr->n_outliers;
+        few = F0.a.out_idx != nullptr && nout <= F0.a.out_capacity && nout <= (unsigned long long)NT;
+        if (few && threadIdx.x < nout) {
+            const uint32_t g = __ldg(F0.a.out_idx + threadIdx.x);
+            const uint32_t plane = (uint32_t)F0.f.n[1] * (uint32_t)F0.f.n[2];
+            oz = (int)(g / plane);
+            const uint32_t r = g - (uint32_t)oz * plane;
+            oy = (int)(r / (uint32_t)F0.f.n[2]);
+            ox = (int)(r - (uint32_t)oy * (uint32_t)F0.f.n[2]);
+        }
+    }
     int lv_field = -1;
     float anc = 0.0f;
     bool anc_ok;
@@ -1238,11 +1256,17 @@ __global__ void __launch_bounds__(NT, kDecompressCtas) k_decompress(const __grid
             const int nfi = MULTI ? nx.fi : 0;
             anc_ok = anchor_fetch(B.fld[nfi], sn, anc);
         }
-        __syncthreads();  // landed codes visible (cp.async: every thread's copies waited for)
+        const bool mine = oz >= sl.g0[0] && oz < sl.g0[0] + EZ && oy >= sl.g0[1] && oy < sl.g0[1] + EY &&
+                          ox >= sl.g0[2] && ox < sl.g0[2] + EX;
+        // landed codes visible (cp.async: every thread's copies waited for), anchors and levels
+        // too; and whether the slab's box may hold an outlier
+        const bool scan = __syncthreads_or(!few || mine) != 0;
         // ---- outliers (code 0): their stored values, scattered into xrec, go into the box
-        if (lv.dense_out) land_outliers<true>(box, land, F, sl);
-        else land_outliers<false>(box, land, F, sl);
-        __syncthreads();  // outlier values, anchors and levels ready
+        if (scan) {
+            if (lv.dense_out) land_outliers<true>(box, land, F, sl);
+            else land_outliers<false>(box, land, F, sl);
+            __syncthreads();  // outlier values in the box
+        }
         if (abort_flag) break;
 
         const Sink sk{nullptr, land, nullptr, nullptr};
